@@ -1,0 +1,567 @@
+/*
+ * oracle.c -- plain, slow, CPU reference for the micro-CT preview hot path.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only tests/, __graft_entry__.smoke()
+ * and bench.py's cpu_baseline / reference leg may load this library.  It shares
+ * no source, header, table or helper with the CUDA library; the two meet only
+ * through the seeded inputs the phantom module writes.
+ *
+ * Paper: "Low-latency Visual Previews of Large Synchrotron Micro-CT Datasets"
+ * (arXiv 2311.15038).  Every function cites the passage it follows.  Where the
+ * paper is silent or garbled the reading taken is stated beside the code.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add, so each
+ * float/double operation is one IEEE rounding, as written).
+ *
+ * Pins (tests/test_oracle_*.py, CPU only):
+ *   orc_histogram   numpy.bincount, count invariant, z-range slabs
+ *   orc_otsu        brute-force minimum of the within-class variance (Eq. 1),
+ *                   two-delta closed form, hand-derived golden histogram
+ *   orc_its         two-delta / symmetric closed forms, hand-derived golden run
+ *   orc_keep_*      hand-built volumes (threshold and top-slab keep tables)
+ *   orc_filter      vectorised numpy restatement on random volumes, idempotence
+ *   orc_downsample  pure-Python brute force on tiny odd sizes, constant volume,
+ *                   exact 2x case via numpy reshape-sum, identity at factor 1
+ *   orc_atlas_pack  hand-placed golden atlas, round trip
+ *   orc_render      Beer-Lambert slab closed form, axis-aligned views against a
+ *                   product-form compositor over scipy map_coordinates samples,
+ *                   empty volume, mirror symmetry of opposite views
+ * No function here is "parity unpinned".
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+
+/* ---------------------------------------------------------------- helpers */
+
+static int orc_log2_exact(int64_t v)
+{
+    int k = 0;
+    if (v <= 0 || (v & (v - 1)) != 0) return -1;
+    while ((1LL << k) < v) ++k;
+    return k;
+}
+
+static uint32_t load_voxel(const void *base, int esize, int64_t idx)
+{
+    if (esize == 1) return ((const uint8_t *)base)[idx];
+    return ((const uint16_t *)base)[idx];
+}
+
+static void store_voxel(void *base, int esize, int64_t idx, uint32_t v)
+{
+    if (esize == 1) ((uint8_t *)base)[idx] = (uint8_t)v;
+    else ((uint16_t *)base)[idx] = (uint16_t)v;
+}
+
+/* Shift that maps a grey value of `bits` bits onto `nbins` bins (nbins a power
+ * of two, 1 <= nbins <= 2^bits).  Returns -1 when the pair is not allowed. */
+static int bin_shift(int bits, int nbins)
+{
+    int lb = orc_log2_exact(nbins);
+    if (bits < 1 || bits > 16 || lb < 0 || lb > bits) return -1;
+    return bits - lb;
+}
+
+/* --------------------------------------------------------------- histogram */
+
+/*
+ * Voxel histogram: the per-grey-value counts that Alg. 1 and Alg. 2 partition
+ * (Sec. III-A) and that the histogram filter inspects (Sec. III-D).
+ * hist[b] = #{voxels with z in [z0,z1) and (v >> shift) == b}, shift =
+ * bits - log2(nbins).  Values >= 2^bits are not grey values of the declared
+ * depth; they are counted in *overflow instead of a bin.
+ */
+int orc_histogram(const void *vol, int esize, int64_t nx, int64_t ny, int64_t nz,
+                  int bits, int64_t z0, int64_t z1, int nbins,
+                  uint64_t *hist, uint64_t *overflow)
+{
+    int shift = bin_shift(bits, nbins);
+    if (!vol || !hist || !overflow || (esize != 1 && esize != 2) || shift < 0)
+        return ORC_EINVAL;
+    if (esize == 1 && bits > 8) return ORC_EINVAL;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || z0 < 0 || z1 > nz || z0 > z1) return ORC_EINVAL;
+    for (int b = 0; b < nbins; ++b) hist[b] = 0;
+    *overflow = 0;
+    const uint32_t limit = 1u << bits;
+    for (int64_t z = z0; z < z1; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                uint32_t v = load_voxel(vol, esize, (z * ny + y) * nx + x);
+                if (v >= limit) *overflow += 1;
+                else hist[v >> shift] += 1;
+            }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------- Otsu */
+
+/*
+ * Otsu thresholding, Alg. 1 (Sec. III-A).  For every sweep value T the
+ * histogram is split into R_a = bins [0, T) and R_b = bins [T, nbins-1]
+ * (reading of the slices "[0:T]" and "[T:255]": the upper region includes the
+ * last bin).  W = class weight n/N ("density"), U = mean grey value of the
+ * class ("Mean"), sigma = W_a W_b (U_a - U_b)^2, the between-class variance;
+ * the first T with a strictly larger sigma wins (strict ">" of Alg. 1), so
+ * ties keep the lowest T.  A sweep value that leaves a class empty gives no
+ * candidate (its W is 0, so sigma could not beat the initial 0 anyway).
+ * Maximising this sigma is the same as minimising Eq. 1's within-class
+ * variance, because the two add up to the fixed total variance.
+ * Class sums are recomputed from scratch for every T, as the sweep reads.
+ * The FP64 evaluation order below is part of the definition:
+ *   Wa = na/N, Wb = nb/N, Ua = Sa/na, Ub = Sb/nb, d = Ua-Ub,
+ *   sigma = ((Wa*Wb)*d)*d.
+ * Voxels with T <= bin keep their value ("lower limit of the intensity
+ * range", Sec. III-A), so T is returned as a bin index.
+ */
+int orc_otsu(const uint64_t *hist, int nbins, int32_t *T_out, double *sigma_out)
+{
+    if (!hist || !T_out || nbins < 1) return ORC_EINVAL;
+    int32_t T_otsu = 0;
+    double sigma_otsu = 0.0;
+    uint64_t N = 0;
+    for (int b = 0; b < nbins; ++b) N += hist[b];
+    for (int T = 0; T < nbins; ++T) {
+        uint64_t na = 0, nb = 0, Sa = 0, Sb = 0;
+        for (int b = 0; b < T; ++b) { na += hist[b]; Sa += (uint64_t)b * hist[b]; }
+        for (int b = T; b < nbins; ++b) { nb += hist[b]; Sb += (uint64_t)b * hist[b]; }
+        if (na == 0 || nb == 0) continue;
+        double Nd = (double)N;
+        double Wa = (double)na / Nd;
+        double Wb = (double)nb / Nd;
+        double Ua = (double)Sa / (double)na;
+        double Ub = (double)Sb / (double)nb;
+        double d = Ua - Ub;
+        double sigma = ((Wa * Wb) * d) * d;
+        if (sigma > sigma_otsu) { sigma_otsu = sigma; T_otsu = T; }
+    }
+    *T_out = T_otsu;
+    if (sigma_out) *sigma_out = sigma_otsu;
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------------- ITS */
+
+/*
+ * Iterative threshold selection, Alg. 2 (Sec. III-A).
+ *   T_it <- T_start = nbins/2 (the "middle" of the dynamic range).
+ *   repeat: R_a = bins b < T_it, R_b = bins b >= T_it (a real T compares
+ *           against integer bins, so the split index is ceil(T_it));
+ *           mu1, mu2 = mean grey value of R_a, R_b (an empty region takes
+ *           mu = T_it, i.e. it does not pull the threshold);
+ *           T_tmp = (mu1 + mu2) / 2;  r = |T_it - T_tmp|;  T_it = T_tmp
+ *   until r == 0.
+ * Reading of the garbled update "r <- |r - T_tmp|": r is the change of the
+ * threshold between consecutive iterations; r == 0 means mu1 and mu2 no
+ * longer change (Step 5 of the prose).  At most max_iter iterations; if r is
+ * still nonzero then *converged = 0 and the last T_it is used.
+ * Kept voxels are those with bin >= T_it, i.e. bin >= ceil(T_it) = *T_out.
+ */
+int orc_its(const uint64_t *hist, int nbins, int max_iter, int32_t *T_out,
+            int32_t *iters_out, int32_t *converged, double *T_real_out)
+{
+    if (!hist || !T_out || !iters_out || !converged || nbins < 1 || max_iter < 1)
+        return ORC_EINVAL;
+    double T_it = (double)nbins / 2.0;
+    double r = T_it;
+    int iters = 0;
+    while (r != 0.0 && iters < max_iter) {
+        double c = ceil(T_it);
+        int64_t m = c < 0.0 ? 0 : (c > (double)nbins ? nbins : (int64_t)c);
+        uint64_t n1 = 0, n2 = 0, S1 = 0, S2 = 0;
+        for (int64_t b = 0; b < m; ++b) { n1 += hist[b]; S1 += (uint64_t)b * hist[b]; }
+        for (int64_t b = m; b < nbins; ++b) { n2 += hist[b]; S2 += (uint64_t)b * hist[b]; }
+        double mu1 = n1 ? (double)S1 / (double)n1 : T_it;
+        double mu2 = n2 ? (double)S2 / (double)n2 : T_it;
+        double T_tmp = (mu1 + mu2) / 2.0;
+        r = fabs(T_it - T_tmp);
+        T_it = T_tmp;
+        ++iters;
+    }
+    double c = ceil(T_it);
+    *T_out = (int32_t)(c < 0.0 ? 0 : (c > (double)nbins ? nbins : c));
+    *iters_out = iters;
+    *converged = (r == 0.0);
+    if (T_real_out) *T_real_out = T_it;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------ keep tables */
+
+/* Threshold classification (Sec. III-A, binary classification of each voxel):
+ * keep[b] = 1 iff b >= T. */
+int orc_keep_threshold(int nbins, int32_t T, uint8_t *keep)
+{
+    if (!keep || nbins < 1) return ORC_EINVAL;
+    for (int b = 0; b < nbins; ++b) keep[b] = (uint8_t)(b >= T);
+    return ORC_OK;
+}
+
+/* Histogram filtering (Sec. III-D): the histogram of the top slices is the
+ * signature of the surroundings, and those bins are disposed of from the whole
+ * volume.  keep[b] = 1 iff hist_top[b] < kmin (kmin = 1: any occurrence in the
+ * top slab removes the bin). */
+int orc_keep_topslab(const uint64_t *hist_top, int nbins, uint64_t kmin, uint8_t *keep)
+{
+    if (!hist_top || !keep || nbins < 1) return ORC_EINVAL;
+    for (int b = 0; b < nbins; ++b) keep[b] = (uint8_t)(hist_top[b] < kmin);
+    return ORC_OK;
+}
+
+/* ----------------------------------------------------------------- filter */
+
+/* Binary classification applied to the volume (Sec. III-A, Sec. III-D):
+ * out = v when v is a grey value of the declared depth and its bin is kept,
+ * else 0 ("removed" voxels become zero). */
+static uint32_t filter_one(uint32_t v, int bits, int shift, const uint8_t *keep)
+{
+    if (v >= (1u << bits)) return 0;
+    return keep[v >> shift] ? v : 0;
+}
+
+int orc_filter(const void *in, int esize, int64_t nvox, int bits,
+               const uint8_t *keep, int nbins, void *out)
+{
+    int shift = bin_shift(bits, nbins);
+    if (!in || !out || !keep || (esize != 1 && esize != 2) || shift < 0 || nvox < 0)
+        return ORC_EINVAL;
+    for (int64_t i = 0; i < nvox; ++i)
+        store_voxel(out, esize, i, filter_one(load_voxel(in, esize, i), bits, shift, keep));
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------- downsample */
+
+/*
+ * Box downsampling of a volume to a slicemap level (slicemap conversion and
+ * the coarse-then-fine multi-resolution loading, Sec. II and Sec. III; the
+ * filter itself is not given by the paper).  Reading: an integer area box.
+ * Output voxel i along an axis of N source and M output voxels covers the
+ * source range [floor(i N / M), floor((i+1) N / M)); the output is the mean of
+ * the covered (optionally keep-filtered) voxels rounded half up,
+ * floor((sum + cnt/2) / cnt) with cnt the box volume.  M <= N on every axis.
+ * With keep == NULL the voxels are used as stored.
+ * Levels k >= 1 of a slicemap are this function applied to level k-1 with
+ * M = N/2 (an exact 2x2x2 box).
+ */
+int orc_downsample(const void *in, int esize, int64_t nx, int64_t ny, int64_t nz,
+                   int bits, const uint8_t *keep, int nbins,
+                   int64_t mx, int64_t my, int64_t mz, void *out)
+{
+    int shift = 0;
+    if (!in || !out || (esize != 1 && esize != 2)) return ORC_EINVAL;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || mx <= 0 || my <= 0 || mz <= 0) return ORC_EINVAL;
+    if (mx > nx || my > ny || mz > nz) return ORC_EINVAL;
+    if (keep) {
+        shift = bin_shift(bits, nbins);
+        if (shift < 0) return ORC_EINVAL;
+    }
+    for (int64_t k = 0; k < mz; ++k) {
+        int64_t z_lo = (k * nz) / mz, z_hi = ((k + 1) * nz) / mz;
+        for (int64_t j = 0; j < my; ++j) {
+            int64_t y_lo = (j * ny) / my, y_hi = ((j + 1) * ny) / my;
+            for (int64_t i = 0; i < mx; ++i) {
+                int64_t x_lo = (i * nx) / mx, x_hi = ((i + 1) * nx) / mx;
+                uint64_t sum = 0;
+                uint64_t cnt = (uint64_t)((z_hi - z_lo) * (y_hi - y_lo) * (x_hi - x_lo));
+                for (int64_t z = z_lo; z < z_hi; ++z)
+                    for (int64_t y = y_lo; y < y_hi; ++y)
+                        for (int64_t x = x_lo; x < x_hi; ++x) {
+                            uint32_t v = load_voxel(in, esize, (z * ny + y) * nx + x);
+                            if (keep) v = filter_one(v, bits, shift, keep);
+                            sum += v;
+                        }
+                store_voxel(out, esize, (k * my + j) * mx + i,
+                            (uint32_t)((sum + cnt / 2) / cnt));
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ atlas */
+
+/*
+ * Slicemap atlas (the 2D grid of tiled slices the paper's previews load,
+ * Sec. III).  Slice z of an mx*my*mz level goes to tile row z / tiles_x, tile
+ * column z % tiles_x; its pixel (x, y) sits at
+ *   atlas[(row*my + y) * (tiles_x*mx) + col*mx + x].
+ * Tiles past the last slice are zero.  tiles_x * tiles_y >= mz.
+ */
+int orc_atlas_pack(const void *level, int esize, int64_t mx, int64_t my, int64_t mz,
+                   int64_t tiles_x, int64_t tiles_y, void *atlas)
+{
+    if (!level || !atlas || (esize != 1 && esize != 2)) return ORC_EINVAL;
+    if (mx <= 0 || my <= 0 || mz <= 0 || tiles_x <= 0 || tiles_y <= 0 || tiles_x * tiles_y < mz)
+        return ORC_EINVAL;
+    int64_t aw = tiles_x * mx, ah = tiles_y * my;
+    memset(atlas, 0, (size_t)(aw * ah * esize));
+    for (int64_t z = 0; z < mz; ++z) {
+        int64_t row = z / tiles_x, col = z % tiles_x;
+        for (int64_t y = 0; y < my; ++y)
+            for (int64_t x = 0; x < mx; ++x)
+                store_voxel(atlas, esize, (row * my + y) * aw + col * mx + x,
+                            load_voxel(level, esize, (z * my + y) * mx + x));
+    }
+    return ORC_OK;
+}
+
+/* ----------------------------------------------------------------- render */
+
+/*
+ * Server-side rendering of a slicemap level to a 2D image (Sec. III-C).  The
+ * paper names the step but not the renderer; this is orthographic
+ * emission-absorption direct volume rendering, front to back:
+ *
+ * Camera (world unit = one source voxel, box [0,Nx]x[0,Ny]x[0,Nz], centre c):
+ *   az, el in radians = (deg * pi) / 180 in FP64;
+ *   b  = (cos el cos az, cos el sin az, sin el)   (towards the viewer)
+ *   r  = (-sin az, cos az, 0)                      (image right)
+ *   u  = (-sin el cos az, -sin el sin az, cos el)  (image up, = b x r)
+ *   each component evaluated in FP64 and rounded to FP32.
+ *   L = FP32(sqrt(Nx^2 + Ny^2 + Nz^2)), the side of the square image plane.
+ * Ray of pixel (i, j), row j counted from the top, all in FP32 with one
+ * rounding per operation, in exactly this order:
+ *   sx = (i + 0.5) / W - 0.5;   sy = 0.5 - (j + 0.5) / H
+ *   o_a = ((c_a + (sx*L)*r_a) + (sy*L)*u_a) + L*b_a;   d_a = -b_a
+ *   slab per axis: d_a != 0: inv = 1/d_a, t0 = (0 - o_a)*inv,
+ *                  t1 = (N_a - o_a)*inv, [min, max];
+ *                  d_a == 0: whole line if 0 <= o_a <= N_a, else no hit
+ *   t_near = max of the mins, t_far = min of the maxes
+ *   s_a = N_a / M_a,  Delta = step * min(s_x, s_y, s_z)
+ *   n = floor((t_far - t_near) / Delta) if t_far > t_near, else 0
+ * Samples (FP64 from here on): t_k = t_near + (k + 1/2) Delta, k < n;
+ *   p = o + t_k d;  level coordinate q_a = (p_a * M_a) / N_a - 1/2;
+ *   trilinear interpolation of the level with corner indices clamped to
+ *   [0, M_a - 1]; value v = min(raw / (2^bits - 1), 1).
+ * Transfer function: nlut >= 2 RGBA entries, x = v (nlut - 1),
+ *   j = min(floor(x), nlut - 2), f = x - j, rgba = lut[j](1-f) + lut[j+1] f.
+ * Compositing (colour in the LUT is straight, the output premultiplied):
+ *   w = (1 - A) alpha;  C += w c;  A += w;  stop once A >= alpha_stop.
+ *
+ * Several results are correct when A lands near alpha_stop, because an FP32
+ * march may stop one sample earlier or later than this FP64 one.  The march
+ * therefore records the state at three stop levels, alpha_stop - eps,
+ * alpha_stop and alpha_stop + eps (rgba_lo, rgba, rgba_hi; nsamp gives the
+ * sample counts at the three levels).  A ray whose lo and hi results differ is
+ * ambiguous; any stop between them is a correct result.
+ */
+typedef struct {
+    float az_deg, el_deg;
+    int32_t width, height;
+    float step;
+} orc_view;
+
+typedef struct {
+    float o[3], d[3];
+    float t_near, delta;
+    int64_t n;
+} orc_ray;
+
+static void ray_setup(const float b[3], const float r[3], const float u[3], float L,
+                      const float c[3], const float N[3], float delta,
+                      int32_t W, int32_t H, int64_t i, int64_t j, orc_ray *ray)
+{
+    float sx = ((float)i + 0.5f) / (float)W - 0.5f;
+    float sy = 0.5f - ((float)j + 0.5f) / (float)H;
+    float sxL = sx * L, syL = sy * L;
+    float tmin = -INFINITY, tmax = INFINITY;
+    int miss = 0;
+    for (int a = 0; a < 3; ++a) {
+        float t1 = c[a] + sxL * r[a];
+        float t2 = t1 + syL * u[a];
+        float oa = t2 + L * b[a];
+        float da = -b[a];
+        ray->o[a] = oa;
+        ray->d[a] = da;
+        if (da != 0.0f) {
+            float inv = 1.0f / da;
+            float s0 = (0.0f - oa) * inv;
+            float s1 = (N[a] - oa) * inv;
+            tmin = fmaxf(tmin, fminf(s0, s1));
+            tmax = fminf(tmax, fmaxf(s0, s1));
+        } else if (!(oa >= 0.0f && oa <= N[a])) {
+            miss = 1;
+        }
+    }
+    ray->t_near = tmin;
+    ray->delta = delta;
+    ray->n = 0;
+    if (!miss && tmax > tmin) {
+        float fn = floorf((tmax - tmin) / delta);
+        ray->n = (int64_t)fn;
+    }
+}
+
+static double level_fetch(const void *lv, int esize, int64_t mx, int64_t my,
+                          int64_t x, int64_t y, int64_t z)
+{
+    return (double)load_voxel(lv, esize, (z * my + y) * mx + x);
+}
+
+static int64_t clampi(int64_t v, int64_t lo, int64_t hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+static double sample_level(const void *lv, int esize, const int64_t M[3], const double q[3],
+                           double vmax)
+{
+    int64_t i0[3], i1[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(q[a]);
+        f[a] = q[a] - fl;
+        i0[a] = clampi((int64_t)fl, 0, M[a] - 1);
+        i1[a] = clampi((int64_t)fl + 1, 0, M[a] - 1);
+    }
+    double c00 = level_fetch(lv, esize, M[0], M[1], i0[0], i0[1], i0[2]) * (1.0 - f[0]) +
+                 level_fetch(lv, esize, M[0], M[1], i1[0], i0[1], i0[2]) * f[0];
+    double c10 = level_fetch(lv, esize, M[0], M[1], i0[0], i1[1], i0[2]) * (1.0 - f[0]) +
+                 level_fetch(lv, esize, M[0], M[1], i1[0], i1[1], i0[2]) * f[0];
+    double c01 = level_fetch(lv, esize, M[0], M[1], i0[0], i0[1], i1[2]) * (1.0 - f[0]) +
+                 level_fetch(lv, esize, M[0], M[1], i1[0], i0[1], i1[2]) * f[0];
+    double c11 = level_fetch(lv, esize, M[0], M[1], i0[0], i1[1], i1[2]) * (1.0 - f[0]) +
+                 level_fetch(lv, esize, M[0], M[1], i1[0], i1[1], i1[2]) * f[0];
+    double c0 = c00 * (1.0 - f[1]) + c10 * f[1];
+    double c1 = c01 * (1.0 - f[1]) + c11 * f[1];
+    double v = (c0 * (1.0 - f[2]) + c1 * f[2]) / vmax;
+    return v > 1.0 ? 1.0 : v;
+}
+
+int orc_render(const void *level, int esize, int bits, int64_t mx, int64_t my, int64_t mz,
+               int64_t nx, int64_t ny, int64_t nz, const float *lut, int nlut,
+               float alpha_stop, double eps, const orc_view *view,
+               const int64_t *pixels, int64_t npix,
+               double *rgba, double *rgba_lo, double *rgba_hi, uint64_t *nsamp)
+{
+    if (!level || !lut || !view || !rgba || (esize != 1 && esize != 2) || nlut < 2) return ORC_EINVAL;
+    if (bits < 1 || bits > 16 || (esize == 1 && bits > 8)) return ORC_EINVAL;
+    if (mx <= 0 || my <= 0 || mz <= 0 || nx <= 0 || ny <= 0 || nz <= 0) return ORC_EINVAL;
+    if (view->width <= 0 || view->height <= 0 || !(view->step > 0.0f)) return ORC_EINVAL;
+    const double PI = 3.14159265358979323846;
+    double az = ((double)view->az_deg * PI) / 180.0;
+    double el = ((double)view->el_deg * PI) / 180.0;
+    float b[3] = {(float)(cos(el) * cos(az)), (float)(cos(el) * sin(az)), (float)sin(el)};
+    float r[3] = {(float)(-sin(az)), (float)cos(az), 0.0f};
+    float u[3] = {(float)(-sin(el) * cos(az)), (float)(-sin(el) * sin(az)), (float)cos(el)};
+    float L = (float)sqrt((double)(nx * nx + ny * ny + nz * nz));
+    float N[3] = {(float)nx, (float)ny, (float)nz};
+    float c[3] = {N[0] / 2.0f, N[1] / 2.0f, N[2] / 2.0f};
+    float s[3] = {N[0] / (float)mx, N[1] / (float)my, N[2] / (float)mz};
+    float smin = fminf(s[0], fminf(s[1], s[2]));
+    float delta = view->step * smin;
+    const int64_t M[3] = {mx, my, mz};
+    const double Nd[3] = {(double)nx, (double)ny, (double)nz};
+    const double vmax = (double)((1u << bits) - 1u);
+    const int64_t W = view->width, H = view->height;
+    const int64_t total = npix >= 0 && pixels ? npix : W * H;
+    const double stops[3] = {(double)alpha_stop - eps, (double)alpha_stop, (double)alpha_stop + eps};
+
+    for (int64_t p = 0; p < total; ++p) {
+        int64_t lin = pixels ? pixels[p] : p;
+        if (lin < 0 || lin >= W * H) return ORC_EINVAL;
+        orc_ray ray;
+        ray_setup(b, r, u, L, c, N, delta, view->width, view->height, lin % W, lin / W, &ray);
+        double C[3] = {0, 0, 0}, A = 0.0;
+        double out[3][4];
+        uint64_t cnt[3];
+        int done[3] = {0, 0, 0};
+        int64_t k = 0;
+        for (; k < ray.n && !done[2]; ++k) {
+            double t = (double)ray.t_near + ((double)k + 0.5) * (double)ray.delta;
+            double q[3];
+            for (int a = 0; a < 3; ++a) {
+                double pa = (double)ray.o[a] + t * (double)ray.d[a];
+                q[a] = (pa * (double)M[a]) / Nd[a] - 0.5;
+            }
+            double v = sample_level(level, esize, M, q, vmax);
+            double x = v * (double)(nlut - 1);
+            double fl = floor(x);
+            int64_t jj = (int64_t)fl;
+            if (jj > nlut - 2) jj = nlut - 2;
+            double f = x - (double)jj;
+            double col[4];
+            for (int ch = 0; ch < 4; ++ch)
+                col[ch] = (double)lut[jj * 4 + ch] * (1.0 - f) + (double)lut[(jj + 1) * 4 + ch] * f;
+            double w = (1.0 - A) * col[3];
+            C[0] += w * col[0];
+            C[1] += w * col[1];
+            C[2] += w * col[2];
+            A += w;
+            for (int s2 = 0; s2 < 3; ++s2) {
+                if (!done[s2] && A >= stops[s2]) {
+                    done[s2] = 1;
+                    out[s2][0] = C[0]; out[s2][1] = C[1]; out[s2][2] = C[2]; out[s2][3] = A;
+                    cnt[s2] = (uint64_t)(k + 1);
+                }
+            }
+        }
+        for (int s2 = 0; s2 < 3; ++s2) {
+            if (!done[s2]) {
+                out[s2][0] = C[0]; out[s2][1] = C[1]; out[s2][2] = C[2]; out[s2][3] = A;
+                cnt[s2] = (uint64_t)k;
+            }
+        }
+        for (int ch = 0; ch < 4; ++ch) {
+            rgba[p * 4 + ch] = out[1][ch];
+            if (rgba_lo) rgba_lo[p * 4 + ch] = out[0][ch];
+            if (rgba_hi) rgba_hi[p * 4 + ch] = out[2][ch];
+        }
+        if (nsamp) { nsamp[p * 3 + 0] = cnt[0]; nsamp[p * 3 + 1] = cnt[1]; nsamp[p * 3 + 2] = cnt[2]; }
+    }
+    return ORC_OK;
+}
+
+/* Ray parameters of one pixel, exposed so the tests can pin the FP32 setup
+ * against closed forms for axis-aligned views. */
+int orc_ray_params(int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny, int64_t nz,
+                   const orc_view *view, int64_t i, int64_t j, float *o, float *d,
+                   float *t_near, float *delta, int64_t *n)
+{
+    if (!view || !o || !d || !t_near || !delta || !n) return ORC_EINVAL;
+    const double PI = 3.14159265358979323846;
+    double az = ((double)view->az_deg * PI) / 180.0;
+    double el = ((double)view->el_deg * PI) / 180.0;
+    float b[3] = {(float)(cos(el) * cos(az)), (float)(cos(el) * sin(az)), (float)sin(el)};
+    float r[3] = {(float)(-sin(az)), (float)cos(az), 0.0f};
+    float u[3] = {(float)(-sin(el) * cos(az)), (float)(-sin(el) * sin(az)), (float)cos(el)};
+    float L = (float)sqrt((double)(nx * nx + ny * ny + nz * nz));
+    float N[3] = {(float)nx, (float)ny, (float)nz};
+    float c[3] = {N[0] / 2.0f, N[1] / 2.0f, N[2] / 2.0f};
+    float s[3] = {N[0] / (float)mx, N[1] / (float)my, N[2] / (float)mz};
+    float smin = fminf(s[0], fminf(s[1], s[2]));
+    orc_ray ray;
+    ray_setup(b, r, u, L, c, N, view->step * smin, view->width, view->height, i, j, &ray);
+    for (int a = 0; a < 3; ++a) { o[a] = ray.o[a]; d[a] = ray.d[a]; }
+    *t_near = ray.t_near;
+    *delta = ray.delta;
+    *n = ray.n;
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- entropy */
+
+/*
+ * Shannon entropy of an image histogram, Eq. 2 (Sec. III-C):
+ * H = -sum_i p_i log2 p_i with p_i the normalised counts; empty bins add 0.
+ */
+int orc_entropy(const uint64_t *counts, int m, double *H_out)
+{
+    if (!counts || !H_out || m < 1) return ORC_EINVAL;
+    uint64_t tot = 0;
+    for (int i = 0; i < m; ++i) tot += counts[i];
+    double H = 0.0;
+    if (tot > 0)
+        for (int i = 0; i < m; ++i)
+            if (counts[i]) {
+                double p = (double)counts[i] / (double)tot;
+                H -= p * log2(p);
+            }
+    *H_out = H;
+    return ORC_OK;
+}
