@@ -1,0 +1,373 @@
+"""Benchmark of the micro-CT preview hot path (one JSON line on rank 0).
+
+A step is one pass of the whole path over the 'full' workload: u16 12-bit
+2016 x 2016 x 1800 phantom (14.6 GB, resident in HBM) -> 4096-bin histogram ->
+Otsu keep table -> fused filter + slicemap levels 512^3 / 256^3 / 128^3 ->
+36-view turntable at 1024 x 1024 (step 0.5, ramp transfer function, early
+exit at alpha 0.99).  value = ray samples marched per second over whole
+steps.  The input (14.6 GB) is larger than L2, so no flush is needed between
+steps.  Multi-GPU runs are independent replicas (weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mctp|reference]
+                  [--workload full|small]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray samples/s + slicemap build HBM GB/s (% of peak); p50/p99 preview latency"
+UNIT = "ray samples/s"
+FP32_FLOPS_PER_SAMPLE = 48       # algorithmic FP32 work of one sample (render roofline)
+
+
+def workload(name: str):
+    import phantom
+    if name == "full":
+        spec = phantom.FULL
+        return dict(spec=spec, bits=12, nbins=4096, level0=(512, 512, 512), nlevels=3, nviews=36, size=1024,
+                    az_step=10.0, desc="full: u16 12-bit 2016x2016x1800 phantom (14.6 GB), 4096 bins, Otsu, "
+                                       "levels 512^3/256^3/128^3, 36-view turntable 1024x1024, step 0.5")
+    spec = phantom.SMALL
+    return dict(spec=spec, bits=8, nbins=256, level0=(128, 128, 128), nlevels=1, nviews=1, size=256,
+                az_step=0.0, desc="small: u8 256^3 phantom, 256 bins, Otsu, level 128^3, 1 view 256x256")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(rows))
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_sample(wl, slab=None):
+    """Time the oracle on a bounded sample of the workload and extrapolate its
+    step time.  Sample: the histogram and slicemap of a 96-slice slab around
+    the middle of the volume, Otsu on that histogram, and 8192 rays of one
+    view aimed at the band of image rows the slab covers (so rays meet
+    objects and exit early as in the full step).  Returns (seconds per full
+    step, ray samples per full step, description)."""
+    import oracle
+    import phantom
+    spec, bits, nbins = wl["spec"], wl["bits"], wl["nbins"]
+    M = wl["level0"]
+    nz_s = min(spec.nz, 96)
+    zs = spec.nz // 2 - nz_s // 2
+    if slab is None:
+        slab = phantom.generate_cpu(spec, ((0, spec.nx), (0, spec.ny), (zs, zs + nz_s)))
+    frac_v = nz_s / spec.nz
+    t0 = time.perf_counter()
+    hist, _ = oracle.histogram(slab, bits, nbins)
+    t_hist = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T, _ = oracle.otsu(hist)
+    t_otsu = time.perf_counter() - t0
+    keep = oracle.keep_threshold(nbins, T)
+    mz_s = max(1, int(round(M[2] * frac_v)))
+    t0 = time.perf_counter()
+    lv = oracle.downsample(slab, bits, (M[0], M[1], mz_s), keep)
+    t_sm = time.perf_counter() - t0
+    level = np.zeros((M[2], M[1], M[0]), lv.dtype)
+    z0 = (M[2] - mz_s) // 2
+    level[z0:z0 + mz_s] = lv
+    size = wl["size"]
+    L = float(np.sqrt(float(spec.nx) ** 2 + float(spec.ny) ** 2 + float(spec.nz) ** 2))
+    half_rows = max(1, int(0.5 * nz_s / (L / size)))
+    rng = np.random.default_rng(0)
+    npix = 8192
+    rows = rng.integers(size // 2 - half_rows, size // 2 + half_rows, size=npix)
+    pix = rows * size + rng.integers(0, size, size=npix)
+    t0 = time.perf_counter()
+    ref = oracle.render(level, bits, (spec.nx, spec.ny, spec.nz), phantom.ramp_lut(256), 30.0, 0.0, size, size,
+                        0.5, 0.99, 0.0, pixels=pix)
+    t_r = time.perf_counter() - t0
+    ns = float(ref["nsamp"][:, 1].sum())
+    rays_full = wl["nviews"] * size ** 2
+    samples_step = ns * rays_full / npix
+    step_s = t_hist / frac_v + t_otsu + t_sm / frac_v + t_r * rays_full / npix
+    text = (f"oracle (C, 1 thread): histogram + slicemap of {nz_s}/{spec.nz} slices, Otsu, {npix} rays "
+            f"({int(ns)} samples) through that slab; extrapolated to one full step; "
+            f"{t_hist + t_otsu + t_sm + t_r:.1f} s measured")
+    return step_s, samples_step, text
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    import phantom
+    phantom.build(gpu=False)
+    spec = wl["spec"]
+    nz_s = min(spec.nz, 96)
+    zs = spec.nz // 2 - nz_s // 2
+    slab = phantom.generate_cpu(spec, ((0, spec.nx), (0, spec.ny), (zs, zs + nz_s)))
+    vals = []
+    text = ""
+    for i in range(args.warmup + args.steps):
+        step_s, samples_step, text = oracle_sample(wl, slab)
+        if i >= args.warmup:
+            vals.append((step_s, samples_step))
+    step_s = statistics.median(v[0] for v in vals)
+    samples = statistics.median(v[1] for v in vals)
+    value = samples / step_s
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=step_s * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="u16/f64", data="synthetic",
+                config=dict(workload=wl["desc"], l2="n/a (CPU)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=text),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- GPU
+
+def run_gpu(args, wl):
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()   # rank 0 built the shared in-tree libraries
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    from paper_2311_15038_gb300 import pipeline as pl
+    mctp._lib.load()
+
+    spec = wl["spec"]
+    dtype = torch.uint8 if spec.esize == 1 else torch.uint16
+    vol = torch.empty(spec.shape, dtype=dtype, device=dev)
+    phantom.generate_gpu(spec, vol)
+    lut = torch.from_numpy(phantom.ramp_lut(256)).to(dev)
+    views = pl.turntable(wl["nviews"], wl["size"], 0, 0.5, 0.0, wl["az_step"] or None)
+    cfg = pl.PreviewConfig((spec.nx, spec.ny, spec.nz), wl["bits"], wl["nbins"], wl["level0"], wl["nlevels"],
+                           views, "otsu", 3, 0.99)
+    stream = torch.cuda.Stream(dev)
+    pipe = pl.PreviewPipeline(cfg, dtype, dev, stream)
+
+    stages = ["histogram", "threshold", "slicemap", "render"]
+    ev = {}
+
+    def timer(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        ev.setdefault(name, []).append(e)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            pipe.run(vol, lut)
+    torch.cuda.synchronize(dev)
+    samples_per_step = int(pipe.samples.item())
+
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    step_events = []
+    t_start.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            pipe.run(vol, lut, timer)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s1.record(stream)
+            step_events.append((s0, s1))
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if ws > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    step_ms = [a.elapsed_time(b) for a, b in step_events]
+    stage_ms = {}
+    for i, name in enumerate(stages):
+        nxt = stages[i + 1] if i + 1 < len(stages) else "end"
+        stage_ms[name] = statistics.mean(a.elapsed_time(b) for a, b in zip(ev[name], ev[nxt]))
+    assert int(pipe.samples.item()) == samples_per_step
+
+    # ---- end to end through the public API: pinned host volume in, images out
+    vol_host = torch.empty(spec.shape, dtype=dtype, pin_memory=True)
+    vol_host.copy_(vol)
+    img_host = torch.empty(pipe.images.shape, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            vol.copy_(vol_host, non_blocking=True)
+            pipe.run(vol, lut)
+            img_host.copy_(pipe.images, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    vol_bytes = spec.nbytes
+    atlas_bytes = sum(a.numel() * a.element_size() for a in pipe.sm.atlases)
+    level0_bytes = pipe.sm.atlases[0].numel() * pipe.sm.atlases[0].element_size()
+    image_bytes = pipe.images.numel() * 4
+    sm_mhz = clk.get("sm_mhz") or pk["sm_max_mhz"]
+    kernels = {
+        "histogram": dict(bound="hbm", bytes=vol_bytes, unit="GB/s"),
+        "slicemap": dict(bound="hbm", bytes=vol_bytes + atlas_bytes, unit="GB/s"),
+        "render": dict(bound="alu", flops=FP32_FLOPS_PER_SAMPLE * samples_per_step, unit="TFLOP/s"),
+        "threshold": dict(bound="alu", flops=0, unit="TFLOP/s"),
+    }
+    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    roof = {}
+    for name, k in kernels.items():
+        t = stage_ms[name] / 1e3
+        if k["bound"] == "hbm":
+            ach = k["bytes"] / t / 1e9
+            roof[name] = dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
+                              frac=ach / pk["hbm_gbs"], ms=stage_ms[name], traffic=None)
+        else:
+            ach = k["flops"] / t / 1e12
+            roof[name] = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s",
+                              frac=ach / fp32_peak, ms=stage_ms[name], traffic=None)
+    roof["render"]["compulsory_hbm_gbs"] = wl["nviews"] * level0_bytes / (stage_ms["render"] / 1e3) / 1e9
+    dominant = max(stage_ms, key=stage_ms.get)
+    steps_total = samples_per_step * args.steps * ws
+    value = steps_total / elapsed
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+        ms_per_step=elapsed * 1e3 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="u16/f32", data="synthetic",
+        config=dict(workload=wl["desc"], l2="inputs larger than L2 (14.6 GB volume; no flush)"
+                    if vol_bytes > 200e6 else "input fits in L2 (L2-resident numbers)",
+                    parallelism=f"replicas x{ws}"),
+        samples_per_step=samples_per_step,
+        slicemap_gbs=roof["slicemap"]["achieved"], slicemap_frac_of_hbm_peak=roof["slicemap"]["frac"],
+        histogram_gbs=roof["histogram"]["achieved"],
+        render_samples_per_s=samples_per_step / (stage_ms["render"] / 1e3),
+        latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
+        stage_ms=stage_ms,
+        roofline=dict(roof[dominant], kernel=dominant, peak_source=pk["source"]),
+        roofline_by_kernel=roof,
+        gpu_launches=4 * args.steps,
+        clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
+        e2e=dict(value=samples_per_step / e2e_s, unit=UNIT, h2d_bytes_per_step=vol_bytes,
+                 d2h_bytes_per_step=image_bytes, ms_per_step=e2e_s * 1e3),
+    )
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nz_s = min(spec.nz, 96)
+        zs = spec.nz // 2 - nz_s // 2
+        del vol_host
+        step_s, samples_step, text = oracle_sample(wl, vol[zs:zs + nz_s].cpu().numpy())
+        line["cpu_baseline"] = dict(value=samples_step / step_s, unit=UNIT, cores=1, kind="oracle", sample=text)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
+    ap.add_argument("--workload", default="full", choices=["full", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * mctp.h -- C ABI of libmctp, the GB300 (sm_103a) micro-CT preview library.
+ *
+ * The library computes the data-parallel hot path of the preview pipeline of
+ * "Low-latency Visual Previews of Large Synchrotron Micro-CT Datasets"
+ * (arXiv 2311.15038): a voxel histogram, threshold selection (Otsu, Alg. 1;
+ * iterative threshold selection, Alg. 2; top-slice histogram filtering,
+ * Sec. III-D), the binary keep/discard classification of voxels (Sec. III-A),
+ * box-filtered multi-resolution slicemap atlases (Sec. II "Interactive
+ * Preview", Sec. III), and server-side direct volume rendering of a slicemap
+ * (Sec. III-C).
+ *
+ * Conventions for every call:
+ *  - Pointers named "device" are CUDA device pointers owned by the caller;
+ *    descriptor structs are host memory read during the call only.  The
+ *    library never keeps a pointer after a call returns and allocates no
+ *    device memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it and the call returns without waiting;
+ *    outputs are valid once the stream has been synchronised.
+ *  - Return value: MCTP_OK, or a negative code from the list below, detected
+ *    on the host before anything is enqueued (MCTP_ECUDA: a launch failed).
+ *  - Volumes are dense [nz][ny][nx] arrays, x fastest:
+ *    voxel (x,y,z) at index (z*ny + y)*nx + x.
+ *  - A grey value has `bits` significant bits; values >= 2^bits are outside
+ *    the declared depth (counted as overflow, never kept by a filter).
+ *  - Histogram bins: nbins is a power of two with 1 <= nbins <= 2^bits, and
+ *    value v falls in bin v >> (bits - log2(nbins)).
+ *  - No call faults or traps on bad input it can see: host checks return an
+ *    error code instead.
+ */
+#ifndef MCTP_H
+#define MCTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCTP_ABI_VERSION 1
+
+/* status codes */
+#define MCTP_OK 0
+#define MCTP_EINVAL (-1)       /* null pointer, bad size, bad nbins, bad level chain */
+#define MCTP_EUNSUPPORTED (-2) /* dtype / bits / mode not supported */
+#define MCTP_ESIZE (-3)        /* atlas tile grid too small, too many views */
+#define MCTP_ECUDA (-4)        /* a CUDA launch or copy failed */
+
+/* voxel types */
+#define MCTP_U8 1
+#define MCTP_U16 2
+
+typedef struct {
+    int64_t nx, ny, nz; /* voxels per axis, each >= 1 */
+    int32_t dtype;      /* MCTP_U8 (bits must be 8) or MCTP_U16 (bits 1..16) */
+    int32_t bits;
+} mctp_volume_desc;
+
+/* threshold selection modes */
+#define MCTP_THR_OTSU 0     /* Alg. 1: keep bins >= T_otsu */
+#define MCTP_THR_ITS 1      /* Alg. 2: keep bins >= ceil(T_it) */
+#define MCTP_THR_TOPSLAB 2  /* Sec. III-D: keep bins absent from the top slices */
+#define MCTP_THR_EXPLICIT 3 /* keep bins >= explicit_T */
+
+typedef struct {
+    int32_t mode;         /* one of MCTP_THR_* */
+    int32_t explicit_T;   /* MCTP_THR_EXPLICIT: first kept bin */
+    int32_t its_max_iter; /* MCTP_THR_ITS: iteration cap, >= 1 (256 is a good default) */
+    int32_t reserved;
+    uint64_t topslab_kmin;/* MCTP_THR_TOPSLAB: a bin is removed once its top-slab count >= kmin (>= 1) */
+} mctp_thr_params;
+
+#define MCTP_MAX_LEVELS 8
+
+/*
+ * A multi-resolution slicemap: level k is an mx*my*mz volume stored as a 2D
+ * atlas of tiles_x * tiles_y tiles of mx*my voxels, one tile per z slice.
+ * Slice z sits in tile row z / tiles_x, column z % tiles_x; voxel (x,y,z) at
+ *   atlas[k][(row*my + y) * (tiles_x*mx) + col*mx + x]
+ * (elements of the source dtype).  Tiles past the last slice are zero.
+ * Level 0 is an area-box reduction of the source volume; level k >= 1 is the
+ * exact 2x2x2 box reduction of level k-1, so its dims are exactly half.
+ * The world box of every level is the source box [0,nx]x[0,ny]x[0,nz].
+ */
+typedef struct {
+    int32_t nlevels;                  /* 1..MCTP_MAX_LEVELS */
+    int32_t dtype;                    /* element type of the atlases (= source dtype) */
+    int32_t bits;                     /* grey-value depth (= source bits) */
+    int32_t reserved;
+    int64_t src_dims[3];              /* nx, ny, nz of the source volume */
+    int32_t dims[MCTP_MAX_LEVELS][3]; /* mx, my, mz of each level */
+    int32_t tiles_x[MCTP_MAX_LEVELS];
+    int32_t tiles_y[MCTP_MAX_LEVELS];
+    void *atlas[MCTP_MAX_LEVELS];     /* device, (tiles_y*my) x (tiles_x*mx) elements each */
+} mctp_slicemap;
+
+/* One orthographic view of a slicemap level.  The camera looks at the centre
+ * of the source box from azimuth az (about +z, from +x) and elevation el;
+ * image right = (-sin az, cos az, 0), image up = (-sin el cos az,
+ * -sin el sin az, cos el); the square image plane has the side of the box
+ * diagonal.  step is the sample spacing in units of the smallest voxel edge
+ * of the level. */
+typedef struct {
+    float azimuth_deg;
+    float elevation_deg;
+    int32_t width, height; /* pixels, >= 1 */
+    int32_t level;         /* slicemap level to render */
+    float step;            /* > 0; 0.5 = half a level voxel */
+} mctp_view;
+
+/*
+ * Voxel histogram (Sec. III-A: the grey-value histogram that Alg. 1 and
+ * Alg. 2 partition; Sec. III-D: the histogram of the top slices).
+ *   vol       device, the volume described by *d
+ *   z0, z1    slab of slices counted, 0 <= z0 <= z1 <= nz (z1 == z0: empty)
+ *   hist      device uint64[nbins], overwritten with the counts
+ *   overflow  device uint64[1], overwritten with the number of values >= 2^bits
+ * Errors: MCTP_EINVAL (null pointers, dims < 1, bad slab, bad nbins),
+ *         MCTP_EUNSUPPORTED (dtype/bits).
+ */
+int mctp_build_histogram(const void *vol, const mctp_volume_desc *d, int64_t z0, int64_t z1,
+                         int32_t nbins, uint64_t *hist, uint64_t *overflow, void *stream);
+
+/*
+ * Threshold selection -> keep table (Sec. III-A, Alg. 1 and Alg. 2;
+ * Sec. III-D histogram filtering).  Computed on the device in FP64 with a
+ * fixed evaluation order:
+ *   OTSU      T = first bin maximising W_a W_b (U_a - U_b)^2 over the split
+ *             [0,T) | [T,nbins); keep[b] = b >= T
+ *   ITS       T_it from nbins/2, T_it <- (mu1 + mu2)/2 until it no longer
+ *             changes (empty side: mu = T_it) or its_max_iter iterations;
+ *             keep[b] = b >= ceil(T_it)
+ *   TOPSLAB   `hist` is the histogram of the top slices; keep[b] =
+ *             hist[b] < topslab_kmin
+ *   EXPLICIT  keep[b] = b >= explicit_T (`hist` may be NULL)
+ *   hist      device uint64[nbins]
+ *   keep_lut  device uint8[nbins], overwritten with 0/1
+ *   result    device int32[4] or NULL: {T (-1 for TOPSLAB), iterations,
+ *             converged (1/0), 0}
+ * Errors: MCTP_EINVAL (null pointers, nbins < 1 or not a power of two,
+ *         nbins > 65536, its_max_iter < 1, kmin < 1), MCTP_EUNSUPPORTED (mode).
+ */
+int mctp_select_threshold(const uint64_t *hist, int32_t nbins, const mctp_thr_params *p,
+                          uint8_t *keep_lut, int32_t *result, void *stream);
+
+/*
+ * Binary classification of every voxel (Sec. III-A; bins disposed of by the
+ * histogram filter, Sec. III-D): out[i] = in[i] if in[i] < 2^bits and
+ * keep_lut[bin(in[i])] != 0, else 0.
+ *   in, out   device volumes described by *d; out may equal in (in place),
+ *             other overlaps are not allowed
+ *   keep_lut  device uint8[nbins]
+ * Errors: MCTP_EINVAL, MCTP_EUNSUPPORTED.
+ */
+int mctp_filter_threshold(const void *in, const mctp_volume_desc *d, const uint8_t *keep_lut,
+                          int32_t nbins, void *out, void *stream);
+
+/*
+ * Multi-resolution slicemap (Sec. III: slices converted into slicemaps;
+ * Sec. II: a coarse dataset is shown before the full one).  Level 0 voxel i
+ * along an axis of n source and m level voxels covers source voxels
+ * [floor(i n/m), floor((i+1) n/m)); its value is the mean of the covered
+ * voxels (after the keep table when keep_lut != NULL), rounded half up.
+ * Level k >= 1 is the exact 2x2x2 mean of level k-1, rounded half up.
+ *   vol       device source volume described by *d (read once)
+ *   keep_lut  device uint8[nbins] or NULL (no filtering)
+ *   sm        caller-filled: nlevels, dims, tiles, atlas pointers; sm->dtype,
+ *             sm->bits and sm->src_dims must match *d.  Every atlas is written
+ *             in full (unused tiles zeroed).
+ * Requirements: 1 <= m <= n per axis for level 0; level k dims = level k-1
+ * dims / 2 exactly; tiles_x * tiles_y >= mz per level.
+ * Errors: MCTP_EINVAL (bad chain or pointers), MCTP_ESIZE (tile grid too
+ *         small), MCTP_EUNSUPPORTED.
+ */
+int mctp_build_slicemap(const void *vol, const mctp_volume_desc *d, const uint8_t *keep_lut,
+                        int32_t nbins, const mctp_slicemap *sm, void *stream);
+
+/*
+ * Server-side rendering of slicemap views (Sec. III-C): orthographic
+ * emission-absorption ray marching, front to back, per pixel:
+ *   ray set-up in FP32 with one rounding per operation, in this order:
+ *   sx = (i + 0.5)/W - 0.5, sy = 0.5 - (j + 0.5)/H (j from the top),
+ *   o = ((c + (sx L) r) + (sy L) u) + L b, d = -b, with c the box centre,
+ *   L = |box diagonal|, b = (cos el cos az, cos el sin az, sin el) and the
+ *   basis vectors rounded once from FP64; slab test per axis with
+ *   inv = 1/d_a, t = (0 - o_a) inv and (n_a - o_a) inv; Delta = step *
+ *   min_a(n_a / m_a); n = floor((t_far - t_near) / Delta) samples at
+ *   t_near + (k + 1/2) Delta,
+ *   trilinear interpolation of the level (corner indices clamped to the
+ *   level), v = min(raw / (2^bits - 1), 1), RGBA = linear interpolation of
+ *   lut_rgba at v (nlut - 1), then w = (1 - A) alpha, C += w rgb, A += w,
+ *   stopping once A >= alpha_stop.
+ *   views     host array of nviews views (any mix of sizes and levels)
+ *   lut_rgba  device float[nlut][4], straight (not premultiplied) colour,
+ *             2 <= nlut <= 4096
+ *   out_rgba  device float; view v is an [height][width][4] premultiplied
+ *             RGBA image (row 0 = top) starting after the images of views
+ *             0..v-1
+ *   samples_taken device uint64[1] or NULL: overwritten with the number of
+ *             samples marched over all rays (up to and including the
+ *             early-exit sample)
+ * Errors: MCTP_EINVAL (null pointers, bad view, bad level, nlut out of
+ *         range, alpha_stop not in (0, 1]), MCTP_ESIZE (a view larger than
+ *         2^28 pixels).
+ */
+int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views, int32_t nviews,
+                      const float *lut_rgba, int32_t nlut, float alpha_stop, float *out_rgba,
+                      uint64_t *samples_taken, void *stream);
+
+/* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
+ * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
+int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);
+
+/* Bytes of one atlas: tiles_x*mx * tiles_y*my * element size (0 on bad input). */
+size_t mctp_atlas_bytes(int32_t mx, int32_t my, int32_t tiles_x, int32_t tiles_y, int32_t dtype);
+
+/* Static string for a status code. */
+const char *mctp_status_string(int code);
+
+/* MCTP_ABI_VERSION of the loaded library. */
+int mctp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,212 @@
+"""GB300 micro-CT preview library: Python binding of libmctp (include/mctp.h).
+
+Every function here only marshals arguments (torch CUDA tensors -> device
+pointers, the current CUDA stream) and calls the C ABI of the same name; the
+work runs in the library's sm_103a kernels.  Hot path of "Low-latency Visual
+Previews of Large Synchrotron Micro-CT Datasets" (arXiv 2311.15038):
+histogram (Sec. III-A), threshold selection (Alg. 1, Alg. 2, Sec. III-D),
+keep/discard filter (Sec. III-A), slicemap atlases (Sec. II, III) and
+server-side rendering (Sec. III-C).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib
+from ._lib import MctpError  # noqa: F401
+
+__all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
+           "Slicemap", "View", "default_tiles", "atlas_bytes", "version", "MctpError"]
+
+_DTYPES = {torch.uint8: (_lib.MCTP_U8, 1), torch.uint16: (_lib.MCTP_U16, 2), torch.int16: (_lib.MCTP_U16, 2)}
+_MODES = {"otsu": _lib.MCTP_THR_OTSU, "its": _lib.MCTP_THR_ITS, "topslab": _lib.MCTP_THR_TOPSLAB,
+          "explicit": _lib.MCTP_THR_EXPLICIT}
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    return t
+
+
+def volume_desc(vol: torch.Tensor, bits: int) -> _lib.VolumeDesc:
+    if vol.dim() != 3 or vol.dtype not in _DTYPES:
+        raise ValueError("volume must be a 3-D uint8/uint16 tensor [nz][ny][nx]")
+    nz, ny, nx = vol.shape
+    return _lib.VolumeDesc(nx, ny, nz, _DTYPES[vol.dtype][0], bits)
+
+
+def version() -> int:
+    return _lib.load().mctp_version()
+
+
+def default_tiles(mz: int) -> tuple[int, int]:
+    tx, ty = _lib.C_I32(), _lib.C_I32()
+    _lib.check(_lib.load().mctp_default_tiles(mz, ctypes.byref(tx), ctypes.byref(ty)), "mctp_default_tiles")
+    return tx.value, ty.value
+
+
+def atlas_bytes(mx: int, my: int, tiles_x: int, tiles_y: int, dtype) -> int:
+    return _lib.load().mctp_atlas_bytes(mx, my, tiles_x, tiles_y, _DTYPES[dtype][0])
+
+
+def build_histogram(vol: torch.Tensor, bits: int, nbins: int, z0: int = 0, z1: int | None = None,
+                    hist: torch.Tensor | None = None, overflow: torch.Tensor | None = None, stream=None):
+    """Histogram of slices [z0, z1) -> (hist uint64[nbins], overflow uint64[1]) on the device."""
+    _cuda(vol, "vol")
+    d = volume_desc(vol, bits)
+    z1 = vol.shape[0] if z1 is None else z1
+    if hist is None:
+        hist = torch.empty(nbins, dtype=torch.uint64, device=vol.device)
+    if overflow is None:
+        overflow = torch.empty(1, dtype=torch.uint64, device=vol.device)
+    _lib.check(_lib.load().mctp_build_histogram(_ptr(vol), ctypes.byref(d), z0, z1, nbins, _ptr(hist),
+                                                _ptr(overflow), _stream(stream)), "mctp_build_histogram")
+    return hist, overflow
+
+
+def select_threshold(hist: torch.Tensor | None, nbins: int | None = None, mode: str = "otsu",
+                     explicit_T: int = 0, its_max_iter: int = 256, topslab_kmin: int = 1,
+                     keep: torch.Tensor | None = None, result: torch.Tensor | None = None,
+                     device=None, stream=None):
+    """Keep table from a histogram -> (keep uint8[nbins], result int32[4] = T, iters, converged, 0)."""
+    if hist is not None:
+        _cuda(hist, "hist")
+        nbins = hist.numel() if nbins is None else nbins
+        device = hist.device
+    if nbins is None:
+        raise ValueError("nbins needed without a histogram")
+    p = _lib.ThrParams(_MODES[mode], explicit_T, its_max_iter, 0, topslab_kmin)
+    if keep is None:
+        keep = torch.empty(nbins, dtype=torch.uint8, device=device)
+    if result is None:
+        result = torch.empty(4, dtype=torch.int32, device=device)
+    _lib.check(_lib.load().mctp_select_threshold(_ptr(hist), nbins, ctypes.byref(p), _ptr(keep), _ptr(result),
+                                                 _stream(stream)), "mctp_select_threshold")
+    return keep, result
+
+
+def filter_threshold(vol: torch.Tensor, bits: int, keep: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """Keep/discard every voxel (out may be vol for in place)."""
+    _cuda(vol, "vol")
+    _cuda(keep, "keep")
+    d = volume_desc(vol, bits)
+    if out is None:
+        out = torch.empty_like(vol)
+    _lib.check(_lib.load().mctp_filter_threshold(_ptr(vol), ctypes.byref(d), _ptr(keep), keep.numel(), _ptr(out),
+                                                 _stream(stream)), "mctp_filter_threshold")
+    return out
+
+
+@dataclass
+class Slicemap:
+    """Device atlases of a multi-resolution slicemap plus their geometry."""
+    src_dims: tuple[int, int, int]
+    dims: list[tuple[int, int, int]]
+    tiles: list[tuple[int, int]]
+    atlases: list[torch.Tensor]
+    bits: int
+    dtype: torch.dtype
+    _desc: _lib.SlicemapDesc | None = field(default=None, repr=False)
+
+    @classmethod
+    def allocate(cls, src_dims, level0_dims, nlevels: int, dtype: torch.dtype, bits: int, device="cuda"):
+        dims = [tuple(level0_dims)]
+        for _ in range(1, nlevels):
+            dims.append(tuple(v // 2 for v in dims[-1]))
+        tiles = [default_tiles(d[2]) for d in dims]
+        atlases = [torch.empty((ty * d[1], tx * d[0]), dtype=dtype, device=device)
+                   for d, (tx, ty) in zip(dims, tiles)]
+        return cls(tuple(src_dims), dims, tiles, atlases, bits, dtype)
+
+    def desc(self) -> _lib.SlicemapDesc:
+        s = _lib.SlicemapDesc()
+        s.nlevels = len(self.dims)
+        s.dtype = _DTYPES[self.dtype][0]
+        s.bits = self.bits
+        for a in range(3):
+            s.src_dims[a] = self.src_dims[a]
+        for k, (d, (tx, ty), at) in enumerate(zip(self.dims, self.tiles, self.atlases)):
+            _cuda(at, "atlas")
+            for a in range(3):
+                s.dims[k][a] = d[a]
+            s.tiles_x[k] = tx
+            s.tiles_y[k] = ty
+            s.atlas[k] = at.data_ptr()
+        return s
+
+    @property
+    def nbytes(self) -> int:
+        return sum(a.numel() * a.element_size() for a in self.atlases)
+
+
+def build_slicemap(vol: torch.Tensor, bits: int, sm: Slicemap, keep: torch.Tensor | None = None,
+                   stream=None) -> Slicemap:
+    """Fill sm's atlases from vol (keep table applied first when given)."""
+    _cuda(vol, "vol")
+    d = volume_desc(vol, bits)
+    s = sm.desc()
+    nb = keep.numel() if keep is not None else 0
+    _lib.check(_lib.load().mctp_build_slicemap(_ptr(vol), ctypes.byref(d), _ptr(keep), nb, ctypes.byref(s),
+                                               _stream(stream)), "mctp_build_slicemap")
+    return sm
+
+
+@dataclass(frozen=True)
+class View:
+    azimuth_deg: float
+    elevation_deg: float
+    width: int
+    height: int
+    level: int = 0
+    step: float = 0.5
+
+
+def view_array(views) -> ctypes.Array:
+    arr = (_lib.ViewDesc * max(1, len(views)))()
+    for i, v in enumerate(views):
+        arr[i] = _lib.ViewDesc(v.azimuth_deg, v.elevation_deg, v.width, v.height, v.level, v.step)
+    return arr
+
+
+def render_views(sm: Slicemap, views, lut: torch.Tensor, alpha_stop: float = 0.99,
+                 out: torch.Tensor | None = None, samples: torch.Tensor | None = None, stream=None):
+    """Render views -> (flat float32 RGBA buffer, samples uint64[1]); see images() to split it."""
+    _cuda(lut, "lut")
+    if lut.dtype != torch.float32 or lut.dim() != 2 or lut.shape[1] != 4:
+        raise ValueError("lut must be float32 [n][4]")
+    total = sum(v.width * v.height * 4 for v in views)
+    dev = lut.device
+    if out is None:
+        out = torch.empty(max(total, 4), dtype=torch.float32, device=dev)
+    if samples is None:
+        samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    s = sm.desc()
+    arr = view_array(views)
+    _lib.check(_lib.load().mctp_render_views(ctypes.byref(s), arr, len(views), _ptr(lut), lut.shape[0],
+                                             alpha_stop, _ptr(out), _ptr(samples), _stream(stream)),
+               "mctp_render_views")
+    return out, samples
+
+
+def images(flat: torch.Tensor, views) -> list[torch.Tensor]:
+    """Split a render_views buffer into [H][W][4] images."""
+    out, off = [], 0
+    for v in views:
+        n = v.width * v.height * 4
+        out.append(flat[off:off + n].view(v.height, v.width, 4))
+        off += n
+    return out

@@ -1,0 +1,36 @@
+// api.cu -- small utility entry points of libmctp (version, status strings,
+// atlas geometry).
+#include "mctp_internal.cuh"
+
+extern "C" int mctp_version(void) { return MCTP_ABI_VERSION; }
+
+extern "C" const char *mctp_status_string(int code)
+{
+    switch (code) {
+    case MCTP_OK: return "ok";
+    case MCTP_EINVAL: return "invalid argument";
+    case MCTP_EUNSUPPORTED: return "unsupported dtype, bit depth, mode or size";
+    case MCTP_ESIZE: return "size limit exceeded (atlas tile grid, view size)";
+    case MCTP_ECUDA: return "CUDA launch or copy failed";
+    default: return "unknown status";
+    }
+}
+
+// Atlas grid of a level with mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
+// tiles_y = ceil(mz / tiles_x).
+extern "C" int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y)
+{
+    if (mz < 1 || !tiles_x || !tiles_y) return MCTP_EINVAL;
+    int64_t tx = 1;
+    while (tx * tx < mz) tx *= 2;
+    *tiles_x = int32_t(tx);
+    *tiles_y = int32_t((mz + tx - 1) / tx);
+    return MCTP_OK;
+}
+
+extern "C" size_t mctp_atlas_bytes(int32_t mx, int32_t my, int32_t tiles_x, int32_t tiles_y, int32_t dtype)
+{
+    const int es = mctp::elem_size(dtype);
+    if (mx < 1 || my < 1 || tiles_x < 1 || tiles_y < 1 || es == 0) return 0;
+    return size_t(tiles_x) * mx * size_t(tiles_y) * my * es;
+}

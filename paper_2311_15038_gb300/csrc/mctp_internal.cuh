@@ -1,0 +1,88 @@
+// mctp_internal.cuh -- helpers shared by the libmctp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mctp.h"
+
+namespace mctp {
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int log2_exact(int64_t v)
+{
+    if (v <= 0 || (v & (v - 1)) != 0) return -1;
+    int k = 0;
+    while ((int64_t(1) << k) < v) ++k;
+    return k;
+}
+
+inline int elem_size(int32_t dtype) { return dtype == MCTP_U8 ? 1 : (dtype == MCTP_U16 ? 2 : 0); }
+
+// MCTP_OK when dtype/bits describe a supported voxel type.
+inline int check_type(int32_t dtype, int32_t bits)
+{
+    if (dtype == MCTP_U8) return bits == 8 ? MCTP_OK : MCTP_EUNSUPPORTED;
+    if (dtype == MCTP_U16) return (bits >= 1 && bits <= 16) ? MCTP_OK : MCTP_EUNSUPPORTED;
+    return MCTP_EUNSUPPORTED;
+}
+
+inline int check_desc(const mctp_volume_desc *d)
+{
+    if (!d) return MCTP_EINVAL;
+    int rc = check_type(d->dtype, d->bits);
+    if (rc != MCTP_OK) return rc;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return MCTP_EINVAL;
+    if (d->nx > (int64_t(1) << 31) || d->ny > (int64_t(1) << 31) || d->nz > (int64_t(1) << 31))
+        return MCTP_EINVAL;
+    return MCTP_OK;
+}
+
+// Shift from a grey value to its bin, or -1 when nbins is not allowed.
+inline int bin_shift(int32_t bits, int32_t nbins)
+{
+    int lb = log2_exact(nbins);
+    if (lb < 0 || lb > bits) return -1;
+    return bits - lb;
+}
+
+inline int launch_status()
+{
+    return cudaGetLastError() == cudaSuccess ? MCTP_OK : MCTP_ECUDA;
+}
+
+inline int num_sms()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = kNumSMs;
+    }
+    return n;
+}
+
+// 16-byte streaming load that bypasses L1 allocation (data read once).
+__device__ __forceinline__ uint4 ld_stream_v4(const void *p)
+{
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ void st_stream_v4(void *p, uint4 v)
+{
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+}  // namespace mctp

@@ -1,0 +1,300 @@
+// render.cu -- server-side rendering of slicemap views (Sec. III-C):
+// orthographic emission-absorption ray marching, front to back, with
+// trilinear sampling of a slicemap level, a 1D RGBA transfer function and
+// early ray termination.
+//
+// Per ray:
+//  * set-up in FP32 with one rounding per operation in a fixed order (camera
+//    origin, slab intersection, sample count n = floor((t_far - t_near) /
+//    Delta)), so n matches any other IEEE implementation of the same steps;
+//  * the level coordinate of sample k is q0 + k dq; q0 and dq are formed in
+//    FP64 once per ray and held as 32.32 fixed-point integers, so stepping is
+//    an exact integer add and the sample position is accurate to ~1e-9 voxel
+//    (an FP32 position would carry ~3e-5 voxel of rounding at 512 voxels);
+//  * trilinear interpolation of the atlas in FP32 (corner indices clamped to
+//    the level), transfer-function lookup with linear interpolation from
+//    shared memory, premultiplied over-compositing, exit once A >= alpha_stop.
+// A warp covers an 8 x 4 pixel tile and a block 16 x 8 pixels, so the rays of
+// a warp sample neighbouring atlas texels together.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mctp_internal.cuh"
+
+namespace mctp {
+
+int check_slicemap(const mctp_slicemap *sm);
+
+namespace {
+
+constexpr int kMaxViewsPerLaunch = 64;
+constexpr int kTileW = 16, kTileH = 8;
+constexpr int kRenderThreads = kTileW * kTileH;
+constexpr int kMaxLut = 4096;
+
+struct ViewParams {
+    float b[3], r[3], u[3];
+    float c[3], N[3];
+    float L, delta;
+    int32_t W, H;
+    int32_t tiles_w;  // image tiles along x
+    int32_t level;
+    double scale[3];  // level voxels per world unit, M_a / N_a
+    int64_t out_offset;  // in floats
+    int64_t tile_begin;  // first block of this view
+};
+
+struct LevelParams {
+    const void *atlas;
+    int32_t mx, my, mz;
+    int32_t tiles_x;
+    int64_t pitch;  // elements per atlas row
+};
+
+struct RenderParams {
+    int32_t nviews;
+    int32_t nlut;
+    float alpha_stop;
+    float inv_vmax;  // 1 / (2^bits - 1)
+    const float4 *lut;
+    float *out;
+    unsigned long long *samples;
+    LevelParams level[MCTP_MAX_LEVELS];
+    ViewParams view[kMaxViewsPerLaunch];
+};
+
+template <typename T>
+__device__ __forceinline__ float texel(const T *atlas, uint32_t off)
+{
+    return float(__ldg(atlas + off));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_constant__ RenderParams P)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    float4 *lut = reinterpret_cast<float4 *>(smem);
+    uint32_t *slice_off = reinterpret_cast<uint32_t *>(lut + P.nlut);
+
+    // which view this block belongs to
+    int v = 0;
+    while (v + 1 < P.nviews && int64_t(blockIdx.x) >= P.view[v + 1].tile_begin) ++v;
+    const ViewParams &V = P.view[v];
+    const LevelParams &Lv = P.level[V.level];
+
+    for (int i = threadIdx.x; i < P.nlut; i += blockDim.x) lut[i] = P.lut[i];
+    for (int z = threadIdx.x; z < Lv.mz; z += blockDim.x) {
+        const int row = z / Lv.tiles_x, col = z - row * Lv.tiles_x;
+        slice_off[z] = uint32_t(int64_t(row) * Lv.my * Lv.pitch + int64_t(col) * Lv.mx);
+    }
+    __syncthreads();
+
+    const int64_t tile = int64_t(blockIdx.x) - V.tile_begin;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = int(tile % V.tiles_w) * kTileW + (warp & 1) * 8 + (lane & 7);
+    const int py = int(tile / V.tiles_w) * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    const bool active = px < V.W && py < V.H;
+
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t taken = 0;
+    if (active) {
+        // ---- FP32 ray set-up, one rounding per operation, fixed order
+        const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
+        const float sy = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn(float(py), 0.5f), float(V.H)));
+        const float sxL = __fmul_rn(sx, V.L), syL = __fmul_rn(sy, V.L);
+        float o[3], d[3];
+        float tmin = -INFINITY, tmax = INFINITY;
+        bool miss = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float t1 = __fadd_rn(V.c[a], __fmul_rn(sxL, V.r[a]));
+            const float t2 = __fadd_rn(t1, __fmul_rn(syL, V.u[a]));
+            o[a] = __fadd_rn(t2, __fmul_rn(V.L, V.b[a]));
+            d[a] = -V.b[a];
+            if (d[a] != 0.0f) {
+                const float inv = __frcp_rn(d[a]);
+                const float s0 = __fmul_rn(__fsub_rn(0.0f, o[a]), inv);
+                const float s1 = __fmul_rn(__fsub_rn(V.N[a], o[a]), inv);
+                tmin = fmaxf(tmin, fminf(s0, s1));
+                tmax = fminf(tmax, fmaxf(s0, s1));
+            } else if (!(o[a] >= 0.0f && o[a] <= V.N[a])) {
+                miss = true;
+            }
+        }
+        int64_t n = 0;
+        if (!miss && tmax > tmin) n = int64_t(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
+
+        if (n > 0) {
+            // ---- fixed-point level coordinates of sample 0 and the step
+            const double t0 = double(tmin) + 0.5 * double(V.delta);
+            long long U[3], dU[3];
+            int Mm1[3];
+            const int M[3] = {Lv.mx, Lv.my, Lv.mz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double q0 = (double(o[a]) + t0 * double(d[a])) * V.scale[a] - 0.5;
+                const double dq = double(V.delta) * double(d[a]) * V.scale[a];
+                U[a] = __double2ll_rn(q0 * 4294967296.0);
+                dU[a] = __double2ll_rn(dq * 4294967296.0);
+                Mm1[a] = M[a] - 1;
+            }
+            const T *atlas = static_cast<const T *>(Lv.atlas);
+            const uint32_t pitch = uint32_t(Lv.pitch);
+            const float nl1 = float(P.nlut - 1);
+            const int jmax = P.nlut - 2;
+            float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+            int64_t k = 0;
+            while (k < n) {
+                int i0[3], i1[3];
+                float f[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int ii = int(U[a] >> 32);
+                    f[a] = float(uint32_t(U[a])) * 2.3283064365386963e-10f;
+                    i0[a] = min(max(ii, 0), Mm1[a]);
+                    i1[a] = min(max(ii + 1, 0), Mm1[a]);
+                }
+                const uint32_t z0 = slice_off[i0[2]], z1 = slice_off[i1[2]];
+                const uint32_t y0 = uint32_t(i0[1]) * pitch, y1 = uint32_t(i1[1]) * pitch;
+                const uint32_t x0 = uint32_t(i0[0]), x1 = uint32_t(i1[0]);
+                const float v000 = texel(atlas, z0 + y0 + x0), v100 = texel(atlas, z0 + y0 + x1);
+                const float v010 = texel(atlas, z0 + y1 + x0), v110 = texel(atlas, z0 + y1 + x1);
+                const float v001 = texel(atlas, z1 + y0 + x0), v101 = texel(atlas, z1 + y0 + x1);
+                const float v011 = texel(atlas, z1 + y1 + x0), v111 = texel(atlas, z1 + y1 + x1);
+                const float c00 = fmaf(f[0], v100 - v000, v000), c10 = fmaf(f[0], v110 - v010, v010);
+                const float c01 = fmaf(f[0], v101 - v001, v001), c11 = fmaf(f[0], v111 - v011, v011);
+                const float c0 = fmaf(f[1], c10 - c00, c00), c1 = fmaf(f[1], c11 - c01, c01);
+                const float val = fminf(fmaf(f[2], c1 - c0, c0) * P.inv_vmax, 1.0f);
+                const float x = val * nl1;
+                const int j = min(int(x), jmax);
+                const float fl = x - float(j);
+                const float4 e0 = lut[j], e1 = lut[j + 1];
+                const float ca = fmaf(fl, e1.w - e0.w, e0.w);
+                const float w = (1.0f - A) * ca;
+                C0 = fmaf(w, fmaf(fl, e1.x - e0.x, e0.x), C0);
+                C1 = fmaf(w, fmaf(fl, e1.y - e0.y, e0.y), C1);
+                C2 = fmaf(w, fmaf(fl, e1.z - e0.z, e0.z), C2);
+                A += w;
+                ++k;
+                if (A >= P.alpha_stop) break;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) U[a] += dU[a];
+            }
+            acc = make_float4(C0, C1, C2, A);
+            taken = k;
+        }
+        reinterpret_cast<float4 *>(P.out + V.out_offset)[int64_t(py) * V.W + px] = acc;
+    }
+    if (P.samples) {
+        unsigned long long t = (unsigned long long)taken;
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o2);
+        if (lane == 0 && t) atomicAdd(P.samples, t);
+    }
+}
+
+}  // namespace
+}  // namespace mctp
+
+extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views, int32_t nviews,
+                                 const float *lut_rgba, int32_t nlut, float alpha_stop, float *out_rgba,
+                                 uint64_t *samples_taken, void *stream)
+{
+    using namespace mctp;
+    int rc = check_slicemap(sm);
+    if (rc != MCTP_OK) return rc;
+    if (!views || nviews < 0 || !lut_rgba || !out_rgba) return MCTP_EINVAL;
+    if (nlut < 2 || nlut > kMaxLut) return MCTP_EINVAL;
+    if (!(alpha_stop > 0.0f && alpha_stop <= 1.0f)) return MCTP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(lut_rgba) & 15) || (reinterpret_cast<uintptr_t>(out_rgba) & 15))
+        return MCTP_EINVAL;
+    for (int i = 0; i < nviews; ++i) {
+        const mctp_view &w = views[i];
+        if (w.width < 1 || w.height < 1 || w.level < 0 || w.level >= sm->nlevels) return MCTP_EINVAL;
+        if (!(w.step >= 1.0f / 256.0f && w.step <= 64.0f)) return MCTP_EINVAL;
+        if (int64_t(w.width) * w.height > (int64_t(1) << 28)) return MCTP_ESIZE;
+    }
+    cudaStream_t s = as_stream(stream);
+    if (samples_taken && cudaMemsetAsync(samples_taken, 0, sizeof(uint64_t), s) != cudaSuccess) return MCTP_ECUDA;
+    if (nviews == 0) return MCTP_OK;
+
+    RenderParams P{};  // copied into each launch's parameter buffer
+    P.nlut = nlut;
+    P.alpha_stop = alpha_stop;
+    P.inv_vmax = float(1.0 / double((1u << sm->bits) - 1u));
+    P.lut = reinterpret_cast<const float4 *>(lut_rgba);
+    P.samples = reinterpret_cast<unsigned long long *>(samples_taken);
+    int max_mz = 1;
+    for (int k = 0; k < sm->nlevels; ++k) {
+        P.level[k].atlas = sm->atlas[k];
+        P.level[k].mx = sm->dims[k][0];
+        P.level[k].my = sm->dims[k][1];
+        P.level[k].mz = sm->dims[k][2];
+        P.level[k].tiles_x = sm->tiles_x[k];
+        P.level[k].pitch = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
+        if (int64_t(sm->tiles_x[k]) * sm->dims[k][0] * int64_t(sm->tiles_y[k]) * sm->dims[k][1] >
+            (int64_t(1) << 32))
+            return MCTP_ESIZE;  // texel offsets are 32-bit
+        max_mz = std::max(max_mz, sm->dims[k][2]);
+    }
+    if (max_mz > 16384) return MCTP_ESIZE;
+    const double PI = 3.14159265358979323846;
+    const int64_t n3[3] = {sm->src_dims[0], sm->src_dims[1], sm->src_dims[2]};
+    const float L = float(sqrt(double(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2])));
+    const float N[3] = {float(n3[0]), float(n3[1]), float(n3[2])};
+    const size_t smem = size_t(nlut) * sizeof(float4) + size_t(max_mz) * sizeof(uint32_t);
+    auto kern = sm->dtype == MCTP_U8 ? render_kernel<uint8_t> : render_kernel<uint16_t>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return MCTP_ECUDA;
+
+    int64_t out_off = 0;
+    for (int first = 0; first < nviews; first += kMaxViewsPerLaunch) {
+        const int cnt = std::min(kMaxViewsPerLaunch, nviews - first);
+        int64_t tiles = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const mctp_view &w = views[first + i];
+            ViewParams &V = P.view[i];
+            const double az = (double(w.azimuth_deg) * PI) / 180.0;
+            const double el = (double(w.elevation_deg) * PI) / 180.0;
+            V.b[0] = float(cos(el) * cos(az));
+            V.b[1] = float(cos(el) * sin(az));
+            V.b[2] = float(sin(el));
+            V.r[0] = float(-sin(az));
+            V.r[1] = float(cos(az));
+            V.r[2] = 0.0f;
+            V.u[0] = float(-sin(el) * cos(az));
+            V.u[1] = float(-sin(el) * sin(az));
+            V.u[2] = float(cos(el));
+            const int *M = sm->dims[w.level];
+            float sa[3];
+            for (int a = 0; a < 3; ++a) {
+                V.N[a] = N[a];
+                V.c[a] = N[a] / 2.0f;
+                sa[a] = N[a] / float(M[a]);
+                V.scale[a] = double(M[a]) / double(n3[a]);
+            }
+            const float smin = fminf(sa[0], fminf(sa[1], sa[2]));
+            V.delta = w.step * smin;
+            V.L = L;
+            V.W = w.width;
+            V.H = w.height;
+            V.level = w.level;
+            V.tiles_w = (w.width + kTileW - 1) / kTileW;
+            V.out_offset = out_off;
+            V.tile_begin = tiles;
+            tiles += int64_t(V.tiles_w) * ((w.height + kTileH - 1) / kTileH);
+            out_off += int64_t(w.width) * w.height * 4;
+        }
+        if (tiles > 0x7fffffff) return MCTP_ESIZE;
+        P.nviews = cnt;
+        P.out = out_rgba;
+        if (sm->dtype == MCTP_U8) render_kernel<uint8_t><<<unsigned(tiles), kRenderThreads, smem, s>>>(P);
+        else render_kernel<uint16_t><<<unsigned(tiles), kRenderThreads, smem, s>>>(P);
+        rc = launch_status();
+        if (rc != MCTP_OK) return rc;
+    }
+    return MCTP_OK;
+}

@@ -1,0 +1,70 @@
+"""The preview hot path as one reusable object: histogram -> threshold keep
+table -> fused filter + slicemap -> rendered views, all enqueued on one CUDA
+stream with outputs allocated once (arXiv 2311.15038, Table I pipelines:
+thresholding, slicemap conversion, server-side rendering)."""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import Slicemap, View, build_histogram, build_slicemap, render_views, select_threshold
+
+
+@dataclass
+class PreviewConfig:
+    src_dims: tuple[int, int, int]          # nx, ny, nz
+    bits: int
+    nbins: int
+    level0: tuple[int, int, int]
+    nlevels: int
+    views: list[View]
+    mode: str = "otsu"                      # otsu | its | topslab | explicit | none
+    topslab: int = 3                        # slices of the top slab (topslab mode)
+    alpha_stop: float = 0.99
+    explicit_T: int = 0
+
+
+def turntable(n: int, size: int, level: int = 0, step: float = 0.5, elevation: float = 0.0,
+              az_step: float | None = None) -> list[View]:
+    """n views around the z axis: azimuth = k * az_step (default 360/n degrees)."""
+    da = 360.0 / n if az_step is None else az_step
+    return [View(da * k, elevation, size, size, level, step) for k in range(n)]
+
+
+class PreviewPipeline:
+    def __init__(self, cfg: PreviewConfig, dtype: torch.dtype, device="cuda", stream=None):
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.stream = stream
+        nb = cfg.nbins
+        self.hist = torch.empty(nb, dtype=torch.uint64, device=self.device)
+        self.overflow = torch.empty(1, dtype=torch.uint64, device=self.device)
+        self.keep = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.result = torch.empty(4, dtype=torch.int32, device=self.device)
+        self.sm = Slicemap.allocate(cfg.src_dims, cfg.level0, cfg.nlevels, dtype, cfg.bits, self.device)
+        total = sum(v.width * v.height * 4 for v in cfg.views)
+        self.images = torch.empty(max(total, 4), dtype=torch.float32, device=self.device)
+        self.samples = torch.empty(1, dtype=torch.uint64, device=self.device)
+
+    def run(self, vol: torch.Tensor, lut: torch.Tensor, timer=None):
+        """Enqueue one pass; `timer(name)` (optional) is called between the steps."""
+        c = self.cfg
+        mark = timer or (lambda name: None)
+        keep = None
+        mark("histogram")
+        if c.mode == "topslab":
+            build_histogram(vol, c.bits, c.nbins, 0, c.topslab, self.hist, self.overflow, self.stream)
+        elif c.mode != "none":
+            build_histogram(vol, c.bits, c.nbins, 0, None, self.hist, self.overflow, self.stream)
+        mark("threshold")
+        if c.mode != "none":
+            select_threshold(self.hist, c.nbins, c.mode, c.explicit_T, keep=self.keep, result=self.result,
+                             stream=self.stream)
+            keep = self.keep
+        mark("slicemap")
+        build_slicemap(vol, c.bits, self.sm, keep, self.stream)
+        mark("render")
+        render_views(self.sm, c.views, lut, c.alpha_stop, self.images, self.samples, self.stream)
+        mark("end")
+        return self.images, self.samples

@@ -1,0 +1,181 @@
+"""The C-ABI library: loads, exports every symbol include/*.h declares, and
+rejects bad arguments on the host before touching a GPU.  No compute calls
+run here (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_15038_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(mctp_\w+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2311_15038_gb300 import _lib
+    names = _declared()
+    assert {"mctp_build_histogram", "mctp_select_threshold", "mctp_filter_threshold", "mctp_build_slicemap",
+            "mctp_render_views"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+        assert n in _lib.EXPORTS, f"{n} has no ctypes signature"
+
+
+def test_host_utilities(lib):
+    assert lib.mctp_version() == 1
+    tx, ty = ctypes.c_int32(), ctypes.c_int32()
+    for mz, want in [(128, (16, 8)), (256, (16, 16)), (512, (32, 16)), (1, (1, 1)), (3, (2, 2))]:
+        assert lib.mctp_default_tiles(mz, ctypes.byref(tx), ctypes.byref(ty)) == 0
+        assert (tx.value, ty.value) == want
+    assert lib.mctp_default_tiles(0, ctypes.byref(tx), ctypes.byref(ty)) == -1
+    assert lib.mctp_atlas_bytes(512, 512, 32, 16, 2) == 16384 * 8192 * 2
+    assert lib.mctp_atlas_bytes(0, 512, 32, 16, 2) == 0
+    assert lib.mctp_atlas_bytes(4, 4, 1, 1, 7) == 0
+    for code in (0, -1, -2, -3, -4):
+        assert lib.mctp_status_string(code)
+    assert lib.mctp_status_string(-99) == b"unknown status"
+
+
+def _desc(nx=8, ny=8, nz=8, dtype=1, bits=8):
+    from paper_2311_15038_gb300 import _lib
+    return _lib.VolumeDesc(nx, ny, nz, dtype, bits)
+
+
+FAKE = ctypes.c_void_p(0x10000)   # never dereferenced: every call below fails its host checks
+
+
+@pytest.mark.parametrize("desc,z0,z1,nbins,want", [
+    (dict(), 0, 8, 256, None),                 # null outputs -> EINVAL (checked separately)
+    (dict(nx=0), 0, 8, 256, -1),
+    (dict(dtype=1, bits=12), 0, 8, 256, -2),
+    (dict(dtype=3), 0, 8, 256, -2),
+    (dict(dtype=2, bits=17), 0, 8, 256, -2),
+    (dict(), 0, 9, 256, -1),
+    (dict(), 5, 4, 256, -1),
+    (dict(), -1, 4, 256, -1),
+    (dict(), 0, 8, 3, -1),
+    (dict(), 0, 8, 512, -1),
+    (dict(dtype=2, bits=12), 0, 8, 8192, -1),
+])
+def test_histogram_rejects(lib, desc, z0, z1, nbins, want):
+    d = _desc(**desc)
+    if want is None:
+        assert lib.mctp_build_histogram(FAKE, ctypes.byref(d), z0, z1, nbins, None, FAKE, None) == -1
+        assert lib.mctp_build_histogram(None, ctypes.byref(d), z0, z1, nbins, FAKE, FAKE, None) == -1
+        assert lib.mctp_build_histogram(FAKE, None, z0, z1, nbins, FAKE, FAKE, None) == -1
+    else:
+        assert lib.mctp_build_histogram(FAKE, ctypes.byref(d), z0, z1, nbins, FAKE, FAKE, None) == want
+
+
+def test_select_threshold_rejects(lib):
+    from paper_2311_15038_gb300 import _lib
+    p = _lib.ThrParams(0, 0, 256, 0, 1)
+    assert lib.mctp_select_threshold(FAKE, 3, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold(FAKE, 0, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold(FAKE, 131072, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold(None, 256, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold(FAKE, 256, ctypes.byref(p), None, None, None) == -1
+    assert lib.mctp_select_threshold(FAKE, 256, None, FAKE, None, None) == -1
+    bad_mode = _lib.ThrParams(9, 0, 256, 0, 1)
+    assert lib.mctp_select_threshold(FAKE, 256, ctypes.byref(bad_mode), FAKE, None, None) == -2
+    its0 = _lib.ThrParams(1, 0, 0, 0, 1)
+    assert lib.mctp_select_threshold(FAKE, 256, ctypes.byref(its0), FAKE, None, None) == -1
+    kmin0 = _lib.ThrParams(2, 0, 256, 0, 0)
+    assert lib.mctp_select_threshold(FAKE, 256, ctypes.byref(kmin0), FAKE, None, None) == -1
+
+
+def test_filter_rejects(lib):
+    d = _desc()
+    assert lib.mctp_filter_threshold(None, ctypes.byref(d), FAKE, 256, FAKE, None) == -1
+    assert lib.mctp_filter_threshold(FAKE, ctypes.byref(d), None, 256, FAKE, None) == -1
+    assert lib.mctp_filter_threshold(FAKE, ctypes.byref(d), FAKE, 100, FAKE, None) == -1
+    # partial overlap of input and output
+    assert lib.mctp_filter_threshold(ctypes.c_void_p(0x10000), ctypes.byref(d), FAKE, 256,
+                                     ctypes.c_void_p(0x10010), None) == -1
+
+
+def _slicemap(levels, src=(64, 64, 64), tiles=None, dtype=1, bits=8):
+    from paper_2311_15038_gb300 import _lib
+    s = _lib.SlicemapDesc()
+    s.nlevels = len(levels)
+    s.dtype, s.bits = dtype, bits
+    for a in range(3):
+        s.src_dims[a] = src[a]
+    for k, d in enumerate(levels):
+        for a in range(3):
+            s.dims[k][a] = d[a]
+        tx, ty = tiles[k] if tiles else (8, 8)
+        s.tiles_x[k], s.tiles_y[k] = tx, ty
+        s.atlas[k] = 0x10000
+    return s
+
+
+@pytest.mark.parametrize("levels,tiles,want", [
+    ([(65, 32, 32)], None, -1),                       # level larger than the source
+    ([(32, 32, 32), (16, 16, 15)], None, -1),        # not an exact halving
+    ([(31, 32, 32), (15, 16, 16)], None, -1),        # odd dimension halved
+    ([(32, 32, 32)], [(4, 4)], -3),                   # 16 tiles for 32 slices
+    ([], None, -1),
+])
+def test_slicemap_rejects(lib, levels, tiles, want):
+    d = _desc(64, 64, 64)
+    s = _slicemap(levels, tiles=tiles)
+    assert lib.mctp_build_slicemap(FAKE, ctypes.byref(d), None, 0, ctypes.byref(s), None) == want
+
+
+def test_slicemap_rejects_mismatched_source(lib):
+    d = _desc(64, 64, 60)
+    s = _slicemap([(32, 32, 32)])
+    assert lib.mctp_build_slicemap(FAKE, ctypes.byref(d), None, 0, ctypes.byref(s), None) == -1
+    d2 = _desc(64, 64, 64, dtype=2, bits=12)
+    assert lib.mctp_build_slicemap(FAKE, ctypes.byref(d2), None, 0, ctypes.byref(s), None) == -1
+
+
+def test_render_rejects(lib):
+    from paper_2311_15038_gb300 import _lib
+    s = _slicemap([(32, 32, 32)])
+    v = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 16, 16, 0, 0.5))
+    ok = dict(views=v, n=1, lut=FAKE, nlut=256, stop=0.99, out=FAKE)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return lib.mctp_render_views(ctypes.byref(s), a["views"], a["n"], a["lut"], a["nlut"], a["stop"],
+                                     a["out"], None, None)
+    assert call(nlut=1) == -1
+    assert call(nlut=5000) == -1
+    assert call(stop=0.0) == -1
+    assert call(stop=1.5) == -1
+    assert call(lut=None) == -1
+    assert call(out=ctypes.c_void_p(0x10004)) == -1                   # misaligned output
+    bad = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 16, 16, 1, 0.5))  # level out of range
+    assert call(views=bad) == -1
+    bad = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 0, 16, 0, 0.5))
+    assert call(views=bad) == -1
+    bad = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 16, 16, 0, 0.0))
+    assert call(views=bad) == -1
+    big = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 1 << 15, 1 << 14, 0, 0.5))
+    assert call(views=big) == -3
+
+
+def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
+    from paper_2311_15038_gb300 import _lib, build
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()
