@@ -94,7 +94,18 @@ typedef struct {
     int32_t tiles_x[MCTP_MAX_LEVELS];
     int32_t tiles_y[MCTP_MAX_LEVELS];
     void *atlas[MCTP_MAX_LEVELS];     /* device, (tiles_y*my) x (tiles_x*mx) elements each */
+    void *maxgrid[MCTP_MAX_LEVELS];   /* device or NULL: per-cell maxima of the level (below) */
 } mctp_slicemap;
+
+/* Occupancy data of a level (an acceleration structure of this library; the
+ * paper has none): maxgrid[k] holds, for every cell of MCTP_MAXGRID_CELL^3
+ * voxels, the maximum over the voxels [c*8, c*8 + 8] per axis (the cell plus
+ * one voxel, clamped to the level) as uint16, cells laid out
+ * [ceil(mz/8)][ceil(my/8)][ceil(mx/8)].  build_slicemap fills it when the
+ * pointer is not NULL; render_views then evaluates only samples whose cell
+ * can reach a transfer-function opacity above zero.  Skipped samples have
+ * opacity exactly zero, so images and sample counts are unchanged. */
+#define MCTP_MAXGRID_CELL 8
 
 /* One orthographic view of a slicemap level.  The camera looks at the centre
  * of the source box from azimuth az (about +z, from +x) and elevation el;
@@ -166,9 +177,10 @@ int mctp_filter_threshold(const void *in, const mctp_volume_desc *d, const uint8
  * Level k >= 1 is the exact 2x2x2 mean of level k-1, rounded half up.
  *   vol       device source volume described by *d (read once)
  *   keep_lut  device uint8[nbins] or NULL (no filtering)
- *   sm        caller-filled: nlevels, dims, tiles, atlas pointers; sm->dtype,
- *             sm->bits and sm->src_dims must match *d.  Every atlas is written
- *             in full (unused tiles zeroed).
+ *   sm        caller-filled: nlevels, dims, tiles, atlas (and optional
+ *             maxgrid) pointers; sm->dtype, sm->bits and sm->src_dims must
+ *             match *d.  Every atlas is written in full (unused tiles zeroed)
+ *             and every non-NULL maxgrid is filled from its level.
  * Requirements: 1 <= m <= n per axis for level 0; level k dims = level k-1
  * dims / 2 exactly; tiles_x * tiles_y >= mz per level.
  * Errors: MCTP_EINVAL (bad chain or pointers), MCTP_ESIZE (tile grid too
@@ -215,6 +227,9 @@ int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);
 
 /* Bytes of one atlas: tiles_x*mx * tiles_y*my * element size (0 on bad input). */
 size_t mctp_atlas_bytes(int32_t mx, int32_t my, int32_t tiles_x, int32_t tiles_y, int32_t dtype);
+
+/* Bytes of one level's maxgrid: ceil(mx/8)*ceil(my/8)*ceil(mz/8)*2 (0 on bad input). */
+size_t mctp_maxgrid_bytes(int32_t mx, int32_t my, int32_t mz);
 
 /* Static string for a status code. */
 const char *mctp_status_string(int code);

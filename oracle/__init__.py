@@ -58,9 +58,10 @@ def _L():
         lib.orc_ray_params.argtypes = [C_I64] * 6 + [ctypes.POINTER(View), C_I64, C_I64,
                                                      C_VP, C_VP, C_VP, C_VP, C_VP]
         lib.orc_entropy.argtypes = [C_VP, ctypes.c_int, C_VP]
+        lib.orc_maxgrid.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, ctypes.c_int, C_VP]
         for f in ("orc_histogram", "orc_otsu", "orc_its", "orc_keep_threshold", "orc_keep_topslab",
                   "orc_filter", "orc_downsample", "orc_atlas_pack", "orc_render", "orc_ray_params",
-                  "orc_entropy"):
+                  "orc_entropy", "orc_maxgrid"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -225,3 +226,12 @@ def entropy(counts: np.ndarray) -> float:
     H = np.zeros(1, np.float64)
     _check(_L().orc_entropy(_p(c), c.size, _p(H)), "entropy")
     return float(H[0])
+
+
+def maxgrid(level: np.ndarray, cell: int = 8) -> np.ndarray:
+    """Per-cell maximum over [cell*c, cell*c + cell] (clamped) of a level [z][y][x]."""
+    level = _vol(level)
+    mz, my, mx = level.shape
+    g = np.zeros((-(-mz // cell), -(-my // cell), -(-mx // cell)), np.uint16)
+    _check(_L().orc_maxgrid(_p(level), level.itemsize, mx, my, mz, cell, _p(g)), "maxgrid")
+    return g

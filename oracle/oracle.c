@@ -20,12 +20,14 @@
  *   orc_its         two-delta / symmetric closed forms, hand-derived golden run
  *   orc_keep_*      hand-built volumes (threshold and top-slab keep tables)
  *   orc_filter      vectorised numpy restatement on random volumes, idempotence
- *   orc_downsample  pure-Python brute force on tiny odd sizes, constant volume,
- *                   exact 2x case via numpy reshape-sum, identity at factor 1
+ *   orc_downsample  numpy block mean for integer factors (incl. identity),
+ *                   constant volume, hot-voxel footprint partition, ramp
+ *                   centres, sum preservation, keep table before averaging
  *   orc_atlas_pack  hand-placed golden atlas, round trip
+ *   orc_maxgrid     scipy.ndimage.maximum_filter on random levels
  *   orc_render      Beer-Lambert slab closed form, axis-aligned views against a
  *                   product-form compositor over scipy map_coordinates samples,
- *                   empty volume, mirror symmetry of opposite views
+ *                   empty volume, axis-aligned sample counts
  * No function here is "parity unpinned".
  */
 #include <math.h>
@@ -541,6 +543,37 @@ int orc_ray_params(int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny, i
     *t_near = ray.t_near;
     *delta = ray.delta;
     *n = ray.n;
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- max grid */
+
+/*
+ * Per-cell maximum of a slicemap level, the occupancy data that lets a
+ * renderer skip samples whose transfer-function opacity is exactly zero (an
+ * acceleration structure of this build; the paper has none).  Cell
+ * (cx, cy, cz) of edge `cell` covers level voxels [cell*c, cell*c + cell] per
+ * axis (one voxel beyond the cell, clamped to the level), i.e. every voxel a
+ * trilinear sample whose lower corner lies in the cell can touch.
+ * grid is [ceil(mz/cell)][ceil(my/cell)][ceil(mx/cell)] uint16.
+ */
+int orc_maxgrid(const void *level, int esize, int64_t mx, int64_t my, int64_t mz, int cell, uint16_t *grid)
+{
+    if (!level || !grid || (esize != 1 && esize != 2) || cell < 1) return ORC_EINVAL;
+    if (mx <= 0 || my <= 0 || mz <= 0) return ORC_EINVAL;
+    int64_t gx = (mx + cell - 1) / cell, gy = (my + cell - 1) / cell, gz = (mz + cell - 1) / cell;
+    for (int64_t cz = 0; cz < gz; ++cz)
+        for (int64_t cy = 0; cy < gy; ++cy)
+            for (int64_t cx = 0; cx < gx; ++cx) {
+                uint32_t m = 0;
+                for (int64_t z = cz * cell; z <= cz * cell + cell && z < mz; ++z)
+                    for (int64_t y = cy * cell; y <= cy * cell + cell && y < my; ++y)
+                        for (int64_t x = cx * cell; x <= cx * cell + cell && x < mx; ++x) {
+                            uint32_t v = load_voxel(level, esize, (z * my + y) * mx + x);
+                            if (v > m) m = v;
+                        }
+                grid[(cz * gy + cy) * gx + cx] = (uint16_t)m;
+            }
     return ORC_OK;
 }
 

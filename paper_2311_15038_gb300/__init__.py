@@ -11,7 +11,7 @@ server-side rendering (Sec. III-C).
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import torch
 
@@ -120,17 +120,23 @@ class Slicemap:
     atlases: list[torch.Tensor]
     bits: int
     dtype: torch.dtype
-    _desc: _lib.SlicemapDesc | None = field(default=None, repr=False)
+    maxgrids: list[torch.Tensor] | None = None
 
     @classmethod
-    def allocate(cls, src_dims, level0_dims, nlevels: int, dtype: torch.dtype, bits: int, device="cuda"):
+    def allocate(cls, src_dims, level0_dims, nlevels: int, dtype: torch.dtype, bits: int, device="cuda",
+                 maxgrid: bool = True):
         dims = [tuple(level0_dims)]
         for _ in range(1, nlevels):
             dims.append(tuple(v // 2 for v in dims[-1]))
         tiles = [default_tiles(d[2]) for d in dims]
         atlases = [torch.empty((ty * d[1], tx * d[0]), dtype=dtype, device=device)
                    for d, (tx, ty) in zip(dims, tiles)]
-        return cls(tuple(src_dims), dims, tiles, atlases, bits, dtype)
+        grids = None
+        if maxgrid:
+            c = _lib.MCTP_MAXGRID_CELL
+            grids = [torch.empty((-(-d[2] // c), -(-d[1] // c), -(-d[0] // c)), dtype=torch.uint16, device=device)
+                     for d in dims]
+        return cls(tuple(src_dims), dims, tiles, atlases, bits, dtype, grids)
 
     def desc(self) -> _lib.SlicemapDesc:
         s = _lib.SlicemapDesc()
@@ -146,7 +152,13 @@ class Slicemap:
             s.tiles_x[k] = tx
             s.tiles_y[k] = ty
             s.atlas[k] = at.data_ptr()
+            if self.maxgrids is not None and self.maxgrids[k] is not None:
+                s.maxgrid[k] = _cuda(self.maxgrids[k], "maxgrid").data_ptr()
         return s
+
+    def without_maxgrid(self) -> "Slicemap":
+        """The same atlases with no occupancy data (renders evaluate every sample)."""
+        return Slicemap(self.src_dims, self.dims, self.tiles, self.atlases, self.bits, self.dtype, None)
 
     @property
     def nbytes(self) -> int:

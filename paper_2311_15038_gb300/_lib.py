@@ -21,6 +21,7 @@ MCTP_THR_TOPSLAB = 2
 MCTP_THR_EXPLICIT = 3
 
 MCTP_MAX_LEVELS = 8
+MCTP_MAXGRID_CELL = 8
 
 C_I32 = ctypes.c_int32
 C_I64 = ctypes.c_int64
@@ -40,7 +41,7 @@ class SlicemapDesc(ctypes.Structure):
     _fields_ = [("nlevels", C_I32), ("dtype", C_I32), ("bits", C_I32), ("reserved", C_I32),
                 ("src_dims", C_I64 * 3), ("dims", (C_I32 * 3) * MCTP_MAX_LEVELS),
                 ("tiles_x", C_I32 * MCTP_MAX_LEVELS), ("tiles_y", C_I32 * MCTP_MAX_LEVELS),
-                ("atlas", C_VP * MCTP_MAX_LEVELS)]
+                ("atlas", C_VP * MCTP_MAX_LEVELS), ("maxgrid", C_VP * MCTP_MAX_LEVELS)]
 
 
 class ViewDesc(ctypes.Structure):
@@ -59,6 +60,7 @@ EXPORTS = {
                            ctypes.c_float, C_VP, C_VP, C_VP], ctypes.c_int),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
+    "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "mctp_version": ([], ctypes.c_int),
 }

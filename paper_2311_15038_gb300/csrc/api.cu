@@ -34,3 +34,10 @@ extern "C" size_t mctp_atlas_bytes(int32_t mx, int32_t my, int32_t tiles_x, int3
     if (mx < 1 || my < 1 || tiles_x < 1 || tiles_y < 1 || es == 0) return 0;
     return size_t(tiles_x) * mx * size_t(tiles_y) * my * es;
 }
+
+extern "C" size_t mctp_maxgrid_bytes(int32_t mx, int32_t my, int32_t mz)
+{
+    if (mx < 1 || my < 1 || mz < 1) return 0;
+    const size_t c = MCTP_MAXGRID_CELL;
+    return ((size_t(mx) + c - 1) / c) * ((size_t(my) + c - 1) / c) * ((size_t(mz) + c - 1) / c) * sizeof(uint16_t);
+}

@@ -14,12 +14,22 @@
 //  * trilinear interpolation of the atlas in FP32 (corner indices clamped to
 //    the level), transfer-function lookup with linear interpolation from
 //    shared memory, premultiplied over-compositing, exit once A >= alpha_stop.
-// A warp covers an 8 x 4 pixel tile and a block 16 x 8 pixels, so the rays of
-// a warp sample neighbouring atlas texels together.
+//
+// Empty-space skipping: when the level has a max grid, every CTA turns it
+// into a shared-memory bitmap of the 8^3 cells that can produce a nonzero
+// opacity under this call's transfer function.  A sample whose lower corner
+// lies in an unmarked cell has opacity exactly 0 (all its corners are at or
+// below a value whose lookup lands on zero-opacity entries, evaluated with the
+// same FP32 operations as a full sample), so it adds exactly nothing to C and
+// A and is not evaluated; images and sample counts equal those of a full
+// march.
+//
+// CTAs are persistent (one wave sized by occupancy) and walk the 16 x 16 pixel
+// tiles of all views in order; a warp covers an 8 x 4 pixel sub-tile so its
+// rays sample neighbouring texels together.
 #include <math.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "mctp_internal.cuh"
 
@@ -30,9 +40,10 @@ int check_slicemap(const mctp_slicemap *sm);
 namespace {
 
 constexpr int kMaxViewsPerLaunch = 64;
-constexpr int kTileW = 16, kTileH = 8;
+constexpr int kTileW = 16, kTileH = 16;
 constexpr int kRenderThreads = kTileW * kTileH;
 constexpr int kMaxLut = 4096;
+constexpr int kMaxBitmapWords = 8192;  // 64^3 cells
 
 struct ViewParams {
     float b[3], r[3], u[3];
@@ -43,14 +54,17 @@ struct ViewParams {
     int32_t level;
     double scale[3];  // level voxels per world unit, M_a / N_a
     int64_t out_offset;  // in floats
-    int64_t tile_begin;  // first block of this view
+    int64_t tile_begin;  // first tile of this view
 };
 
 struct LevelParams {
     const void *atlas;
+    const uint16_t *maxgrid;  // nullptr: no skipping
     int32_t mx, my, mz;
     int32_t tiles_x;
-    int64_t pitch;  // elements per atlas row
+    int32_t gx, gy, gz;       // max-grid cells per axis
+    int32_t pad;
+    int64_t pitch;            // elements per atlas row
 };
 
 struct RenderParams {
@@ -58,6 +72,9 @@ struct RenderParams {
     int32_t nlut;
     float alpha_stop;
     float inv_vmax;  // 1 / (2^bits - 1)
+    int32_t vmax_int;
+    int32_t pad;
+    int64_t total_tiles;
     const float4 *lut;
     float *out;
     unsigned long long *samples;
@@ -71,35 +88,89 @@ __device__ __forceinline__ float texel(const T *atlas, uint32_t off)
     return float(__ldg(atlas + off));
 }
 
+// Lookup coordinate of a raw interpolated value, as the march computes it.
+__device__ __forceinline__ float lut_coord(float raw, float inv_vmax, float nl1)
+{
+    return __fmul_rn(fminf(__fmul_rn(raw, inv_vmax), 1.0f), nl1);
+}
+
+// Largest raw grey value S such that every sample whose corners are all <= S
+// has opacity exactly 0 under the transfer function in shared memory; -1 when
+// none.  Corners <= S give an interpolated value below S + 1, whose lookup
+// coordinate is <= that of S + 1; if that coordinate is <= zmax (entries
+// 0..zmax have zero opacity) the interpolated opacity is exactly 0.  All-zero
+// corners interpolate to exactly 0, which is enough when entry 0 is zero.
+__device__ int skip_threshold(const float4 *lut, int nlut, float inv_vmax, int vmax_int)
+{
+    int zmax = -1;
+    while (zmax + 1 < nlut && lut[zmax + 1].w == 0.0f) ++zmax;
+    if (zmax < 0) return -1;
+    const float nl1 = float(nlut - 1), zf = float(zmax);
+    int lo = -1, hi = vmax_int;  // invariant: lo satisfies (or is -1), hi + 1 fails or hi is the top
+    if (lut_coord(float(vmax_int) + 1.0f, inv_vmax, nl1) <= zf) return vmax_int;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (lut_coord(float(mid) + 1.0f, inv_vmax, nl1) <= zf) lo = mid;
+        else hi = mid;
+    }
+    return max(lo, 0);  // zmax >= 0 means entry 0 is zero, so all-zero cells always skip
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_constant__ RenderParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     float4 *lut = reinterpret_cast<float4 *>(smem);
     uint32_t *slice_off = reinterpret_cast<uint32_t *>(lut + P.nlut);
-
-    // which view this block belongs to
-    int v = 0;
-    while (v + 1 < P.nviews && int64_t(blockIdx.x) >= P.view[v + 1].tile_begin) ++v;
-    const ViewParams &V = P.view[v];
-    const LevelParams &Lv = P.level[V.level];
+    __shared__ uint32_t occ[kMaxBitmapWords];
+    __shared__ int sh_skip;
 
     for (int i = threadIdx.x; i < P.nlut; i += blockDim.x) lut[i] = P.lut[i];
-    for (int z = threadIdx.x; z < Lv.mz; z += blockDim.x) {
-        const int row = z / Lv.tiles_x, col = z - row * Lv.tiles_x;
-        slice_off[z] = uint32_t(int64_t(row) * Lv.my * Lv.pitch + int64_t(col) * Lv.mx);
-    }
     __syncthreads();
+    if (threadIdx.x == 0) sh_skip = skip_threshold(lut, P.nlut, P.inv_vmax, P.vmax_int);
+    __syncthreads();
+    const int skip_S = sh_skip;
 
-    const int64_t tile = int64_t(blockIdx.x) - V.tile_begin;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = int(tile % V.tiles_w) * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int py = int(tile / V.tiles_w) * kTileH + (warp >> 1) * 4 + (lane >> 3);
-    const bool active = px < V.W && py < V.H;
+    unsigned long long taken_total = 0;
+    int v = 0, cur_level = -1;
+    bool use_skip = false;
+    int gx = 0, gy = 0;
 
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int64_t taken = 0;
-    if (active) {
+    for (int64_t tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+        while (v + 1 < P.nviews && tile >= P.view[v + 1].tile_begin) ++v;
+        const ViewParams &V = P.view[v];
+        const LevelParams &Lv = P.level[V.level];
+        if (V.level != cur_level) {  // uniform across the CTA
+            __syncthreads();
+            cur_level = V.level;
+            for (int z = threadIdx.x; z < Lv.mz; z += blockDim.x) {
+                const int row = z / Lv.tiles_x, col = z - row * Lv.tiles_x;
+                slice_off[z] = uint32_t(int64_t(row) * Lv.my * Lv.pitch + int64_t(col) * Lv.mx);
+            }
+            const int64_t ncells = int64_t(Lv.gx) * Lv.gy * Lv.gz;
+            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && ncells <= 32 * kMaxBitmapWords;
+            gx = Lv.gx;
+            gy = Lv.gy;
+            if (use_skip) {
+                const int nwords = int((ncells + 31) / 32);
+                for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+                    uint32_t bits = 0;
+                    for (int b = 0; b < 32; ++b) {
+                        const int64_t c = int64_t(w) * 32 + b;
+                        if (c < ncells && int(__ldg(Lv.maxgrid + c)) > skip_S) bits |= 1u << b;
+                    }
+                    occ[w] = bits;
+                }
+            }
+            __syncthreads();
+        }
+
+        const int64_t t = tile - V.tile_begin;
+        const int px = int(t % V.tiles_w) * kTileW + (warp & 1) * 8 + (lane & 7);
+        const int py = int(t / V.tiles_w) * kTileH + (warp >> 1) * 4 + (lane >> 3);
+        if (px >= V.W || py >= V.H) continue;
+
         // ---- FP32 ray set-up, one rounding per operation, fixed order
         const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
         const float sy = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn(float(py), 0.5f), float(V.H)));
@@ -126,20 +197,19 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
         int64_t n = 0;
         if (!miss && tmax > tmin) n = int64_t(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
 
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (n > 0) {
             // ---- fixed-point level coordinates of sample 0 and the step
             const double t0 = double(tmin) + 0.5 * double(V.delta);
             long long U[3], dU[3];
-            int Mm1[3];
-            const int M[3] = {Lv.mx, Lv.my, Lv.mz};
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double q0 = (double(o[a]) + t0 * double(d[a])) * V.scale[a] - 0.5;
                 const double dq = double(V.delta) * double(d[a]) * V.scale[a];
                 U[a] = __double2ll_rn(q0 * 4294967296.0);
                 dU[a] = __double2ll_rn(dq * 4294967296.0);
-                Mm1[a] = M[a] - 1;
             }
+            const int Mm1x = Lv.mx - 1, Mm1y = Lv.my - 1, Mm1z = Lv.mz - 1;
             const T *atlas = static_cast<const T *>(Lv.atlas);
             const uint32_t pitch = uint32_t(Lv.pitch);
             const float nl1 = float(P.nlut - 1);
@@ -147,27 +217,32 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
             int64_t k = 0;
             while (k < n) {
-                int i0[3], i1[3];
-                float f[3];
+                const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
+                const int x0 = min(max(ix, 0), Mm1x), y0i = min(max(iy, 0), Mm1y), z0i = min(max(iz, 0), Mm1z);
+                if (use_skip) {
+                    const int cell = ((z0i >> 3) * gy + (y0i >> 3)) * gx + (x0 >> 3);
+                    if (!((occ[cell >> 5] >> (cell & 31)) & 1u)) {
+                        ++k;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const int ii = int(U[a] >> 32);
-                    f[a] = float(uint32_t(U[a])) * 2.3283064365386963e-10f;
-                    i0[a] = min(max(ii, 0), Mm1[a]);
-                    i1[a] = min(max(ii + 1, 0), Mm1[a]);
+                        for (int a = 0; a < 3; ++a) U[a] += dU[a];
+                        continue;
+                    }
                 }
-                const uint32_t z0 = slice_off[i0[2]], z1 = slice_off[i1[2]];
-                const uint32_t y0 = uint32_t(i0[1]) * pitch, y1 = uint32_t(i1[1]) * pitch;
-                const uint32_t x0 = uint32_t(i0[0]), x1 = uint32_t(i1[0]);
-                const float v000 = texel(atlas, z0 + y0 + x0), v100 = texel(atlas, z0 + y0 + x1);
-                const float v010 = texel(atlas, z0 + y1 + x0), v110 = texel(atlas, z0 + y1 + x1);
-                const float v001 = texel(atlas, z1 + y0 + x0), v101 = texel(atlas, z1 + y0 + x1);
-                const float v011 = texel(atlas, z1 + y1 + x0), v111 = texel(atlas, z1 + y1 + x1);
-                const float c00 = fmaf(f[0], v100 - v000, v000), c10 = fmaf(f[0], v110 - v010, v010);
-                const float c01 = fmaf(f[0], v101 - v001, v001), c11 = fmaf(f[0], v111 - v011, v011);
-                const float c0 = fmaf(f[1], c10 - c00, c00), c1 = fmaf(f[1], c11 - c01, c01);
-                const float val = fminf(fmaf(f[2], c1 - c0, c0) * P.inv_vmax, 1.0f);
-                const float x = val * nl1;
+                const float fx = float(uint32_t(U[0])) * 2.3283064365386963e-10f;
+                const float fy = float(uint32_t(U[1])) * 2.3283064365386963e-10f;
+                const float fz = float(uint32_t(U[2])) * 2.3283064365386963e-10f;
+                const int x1 = min(max(ix + 1, 0), Mm1x), y1i = min(max(iy + 1, 0), Mm1y);
+                const int z1i = min(max(iz + 1, 0), Mm1z);
+                const uint32_t za = slice_off[z0i], zb = slice_off[z1i];
+                const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
+                const float v000 = texel(atlas, za + ya + x0), v100 = texel(atlas, za + ya + x1);
+                const float v010 = texel(atlas, za + yb + x0), v110 = texel(atlas, za + yb + x1);
+                const float v001 = texel(atlas, zb + ya + x0), v101 = texel(atlas, zb + ya + x1);
+                const float v011 = texel(atlas, zb + yb + x0), v111 = texel(atlas, zb + yb + x1);
+                const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
+                const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
+                const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+                const float x = lut_coord(fmaf(fz, c1 - c0, c0), P.inv_vmax, nl1);
                 const int j = min(int(x), jmax);
                 const float fl = x - float(j);
                 const float4 e0 = lut[j], e1 = lut[j + 1];
@@ -183,12 +258,12 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
                 for (int a = 0; a < 3; ++a) U[a] += dU[a];
             }
             acc = make_float4(C0, C1, C2, A);
-            taken = k;
+            taken_total += (unsigned long long)k;
         }
         reinterpret_cast<float4 *>(P.out + V.out_offset)[int64_t(py) * V.W + px] = acc;
     }
     if (P.samples) {
-        unsigned long long t = (unsigned long long)taken;
+        unsigned long long t = taken_total;
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o2);
         if (lane == 0 && t) atomicAdd(P.samples, t);
@@ -224,16 +299,23 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
     P.nlut = nlut;
     P.alpha_stop = alpha_stop;
     P.inv_vmax = float(1.0 / double((1u << sm->bits) - 1u));
+    P.vmax_int = int((1u << sm->bits) - 1u);
     P.lut = reinterpret_cast<const float4 *>(lut_rgba);
     P.samples = reinterpret_cast<unsigned long long *>(samples_taken);
     int max_mz = 1;
     for (int k = 0; k < sm->nlevels; ++k) {
-        P.level[k].atlas = sm->atlas[k];
-        P.level[k].mx = sm->dims[k][0];
-        P.level[k].my = sm->dims[k][1];
-        P.level[k].mz = sm->dims[k][2];
-        P.level[k].tiles_x = sm->tiles_x[k];
-        P.level[k].pitch = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
+        LevelParams &L = P.level[k];
+        L.atlas = sm->atlas[k];
+        L.maxgrid = static_cast<const uint16_t *>(sm->maxgrid[k]);
+        L.mx = sm->dims[k][0];
+        L.my = sm->dims[k][1];
+        L.mz = sm->dims[k][2];
+        L.tiles_x = sm->tiles_x[k];
+        const int c = MCTP_MAXGRID_CELL;
+        L.gx = (L.mx + c - 1) / c;
+        L.gy = (L.my + c - 1) / c;
+        L.gz = (L.mz + c - 1) / c;
+        L.pitch = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
         if (int64_t(sm->tiles_x[k]) * sm->dims[k][0] * int64_t(sm->tiles_y[k]) * sm->dims[k][1] >
             (int64_t(1) << 32))
             return MCTP_ESIZE;  // texel offsets are 32-bit
@@ -246,9 +328,12 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
     const float N[3] = {float(n3[0]), float(n3[1]), float(n3[2])};
     const size_t smem = size_t(nlut) * sizeof(float4) + size_t(max_mz) * sizeof(uint32_t);
     auto kern = sm->dtype == MCTP_U8 ? render_kernel<uint8_t> : render_kernel<uint16_t>;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return MCTP_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, smem) != cudaSuccess)
+        return MCTP_ECUDA;
+    per_sm = std::max(per_sm, 1);
 
     int64_t out_off = 0;
     for (int first = 0; first < nviews; first += kMaxViewsPerLaunch) {
@@ -288,11 +373,11 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
             tiles += int64_t(V.tiles_w) * ((w.height + kTileH - 1) / kTileH);
             out_off += int64_t(w.width) * w.height * 4;
         }
-        if (tiles > 0x7fffffff) return MCTP_ESIZE;
         P.nviews = cnt;
+        P.total_tiles = tiles;
         P.out = out_rgba;
-        if (sm->dtype == MCTP_U8) render_kernel<uint8_t><<<unsigned(tiles), kRenderThreads, smem, s>>>(P);
-        else render_kernel<uint16_t><<<unsigned(tiles), kRenderThreads, smem, s>>>(P);
+        const int64_t grid = std::min<int64_t>(tiles, int64_t(per_sm) * num_sms());
+        kern<<<unsigned(grid), kRenderThreads, smem, s>>>(P);
         rc = launch_status();
         if (rc != MCTP_OK) return rc;
     }

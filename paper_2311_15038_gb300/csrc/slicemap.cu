@@ -268,6 +268,34 @@ __global__ void __launch_bounds__(256) halve_kernel(const T *__restrict__ src, i
     }
 }
 
+// Per-cell maxima of a level (occupancy data for the renderer): cell c covers
+// voxels [8c, 8c + 8] per axis, clamped.  One block per (cz, cy) row of
+// cells: the 9 x 9 (y, z) atlas rows of the row are read coalesced and their
+// column maxima kept in shared memory, then each cell takes the maximum of
+// its 9 columns.
+template <typename T>
+__global__ void __launch_bounds__(256) maxgrid_kernel(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx,
+                                                      int my, int mz, uint16_t *__restrict__ grid, int gx, int gy)
+{
+    extern __shared__ uint32_t colmax[];
+    const int cy = blockIdx.x % gy, cz = blockIdx.x / gy;
+    const int c = MCTP_MAXGRID_CELL;
+    for (int x = threadIdx.x; x < mx; x += blockDim.x) colmax[x] = 0u;
+    const int z1 = min(cz * c + c, mz - 1), y1 = min(cy * c + c, my - 1);
+    for (int z = cz * c; z <= z1; ++z)
+        for (int y = cy * c; y <= y1; ++y) {
+            const T *row = atlas_ptr(const_cast<T *>(atlas), pitch, tiles_x, mx, my, 0, y, z);
+            for (int x = threadIdx.x; x < mx; x += blockDim.x) colmax[x] = max(colmax[x], uint32_t(__ldg(row + x)));
+        }
+    __syncthreads();
+    for (int cx = threadIdx.x; cx < gx; cx += blockDim.x) {
+        uint32_t m = 0;
+        const int x1 = min(cx * c + c, mx - 1);
+        for (int x = cx * c; x <= x1; ++x) m = max(m, colmax[x]);
+        grid[(int64_t(cz) * gy + cy) * gx + cx] = uint16_t(m);
+    }
+}
+
 // Zero the tiles of an atlas that hold no slice.
 int zero_unused_tiles(void *atlas, int esize, int mx, int my, int mz, int tx, int ty, cudaStream_t s)
 {
@@ -333,6 +361,22 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
     for (int k = 0; k < sm->nlevels; ++k) {
         rc = zero_unused_tiles(sm->atlas[k], int(sizeof(T)), sm->dims[k][0], sm->dims[k][1], sm->dims[k][2],
                                sm->tiles_x[k], sm->tiles_y[k], s);
+        if (rc != MCTP_OK) return rc;
+    }
+    for (int k = 0; k < sm->nlevels; ++k) {
+        if (!sm->maxgrid[k]) continue;
+        const int c = MCTP_MAXGRID_CELL;
+        const int mx = sm->dims[k][0], my = sm->dims[k][1], mz = sm->dims[k][2];
+        const int gx = (mx + c - 1) / c, gy = (my + c - 1) / c, gz = (mz + c - 1) / c;
+        const size_t smem = size_t(mx) * sizeof(uint32_t);
+        if (smem > 200 * 1024) return MCTP_EUNSUPPORTED;
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(maxgrid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     int(smem)) != cudaSuccess)
+            return MCTP_ECUDA;
+        maxgrid_kernel<T><<<unsigned(int64_t(gy) * gz), 256, smem, s>>>(
+            static_cast<const T *>(sm->atlas[k]), int64_t(sm->tiles_x[k]) * mx, sm->tiles_x[k], mx, my, mz,
+            static_cast<uint16_t *>(sm->maxgrid[k]), gx, gy);
+        rc = launch_status();
         if (rc != MCTP_OK) return rc;
     }
     return MCTP_OK;

@@ -47,6 +47,9 @@ def test_host_utilities(lib):
     assert lib.mctp_atlas_bytes(512, 512, 32, 16, 2) == 16384 * 8192 * 2
     assert lib.mctp_atlas_bytes(0, 512, 32, 16, 2) == 0
     assert lib.mctp_atlas_bytes(4, 4, 1, 1, 7) == 0
+    assert lib.mctp_maxgrid_bytes(512, 512, 512) == 64 ** 3 * 2
+    assert lib.mctp_maxgrid_bytes(9, 8, 17) == 2 * 1 * 3 * 2
+    assert lib.mctp_maxgrid_bytes(0, 8, 8) == 0
     for code in (0, -1, -2, -3, -4):
         assert lib.mctp_status_string(code)
     assert lib.mctp_status_string(-99) == b"unknown status"
@@ -123,6 +126,7 @@ def _slicemap(levels, src=(64, 64, 64), tiles=None, dtype=1, bits=8):
         tx, ty = tiles[k] if tiles else (8, 8)
         s.tiles_x[k], s.tiles_y[k] = tx, ty
         s.atlas[k] = 0x10000
+        s.maxgrid[k] = None
     return s
 
 

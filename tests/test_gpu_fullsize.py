@@ -65,6 +65,12 @@ def test_full_workload(capsys):
         got = pipe.sm.atlases[k].cpu().numpy()
         ref = oracle.atlas_pack(lv, tx, ty)
         assert np.array_equal(got, ref), f"level {k}: {(got != ref).sum()} voxels differ"
+        assert np.array_equal(pipe.sm.maxgrids[k].cpu().numpy(), oracle.maxgrid(lv, 8)), f"maxgrid {k}"
+    # empty-space skipping is exact at full size too
+    from paper_2311_15038_gb300 import render_views
+    flat_full, samples_full = render_views(pipe.sm.without_maxgrid(), cfg.views, lut, 0.99)
+    assert torch.equal(flat, flat_full) and int(samples.item()) == int(samples_full.item())
+    del flat_full
 
     from paper_2311_15038_gb300 import images
     imgs = images(flat, cfg.views)

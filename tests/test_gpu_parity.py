@@ -154,6 +154,8 @@ def _check_atlases(sm, levels, oracle, tiles=None):
         got = sm.atlases[k].cpu().numpy()
         assert got.shape == ref.shape, k
         assert np.array_equal(got, ref), f"level {k}: {(got != ref).sum()} voxels differ"
+        if sm.maxgrids is not None:
+            assert np.array_equal(sm.maxgrids[k].cpu().numpy(), oracle.maxgrid(lv, 8)), f"maxgrid {k}"
 
 
 @pytest.mark.parametrize("case", ["small_cfg", "u16_4levels_otsu", "u8_topslab", "scalar_rows", "identity",
@@ -231,7 +233,12 @@ def _render_case(env, vol, bits, dims, views, lut, stop=0.99, keep_mode="otsu", 
                                 torch.from_numpy(vol[:1, :1, :1]).dtype, bits, dev)
     mctp.build_slicemap(g, bits, sm, keep)
     levels = oracle.slicemap(vol, bits, dims, keep_ref)
+    _check_atlases(sm, levels, oracle)
     flat, samples = mctp.render_views(sm, views, up(lut, dev), stop)
+    # skipping zero-opacity cells is exact: the same images and counts as a full march
+    flat_full, samples_full = mctp.render_views(sm.without_maxgrid(), views, up(lut, dev), stop)
+    assert torch.equal(flat, flat_full)
+    assert int(samples.item()) == int(samples_full.item())
     imgs = mctp.images(flat, views)
     lo_tot = hi_tot = 0
     worst = 0.0

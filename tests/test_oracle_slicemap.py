@@ -142,3 +142,16 @@ def test_default_tiles():
     assert oracle.default_tiles(512) == (32, 16)
     assert oracle.default_tiles(1) == (1, 1)
     assert oracle.default_tiles(3) == (2, 2)
+
+
+@pytest.mark.parametrize("shape,cell,dtype", [((16, 24, 40), 8, np.uint16), ((13, 9, 17), 8, np.uint8),
+                                              ((20, 20, 20), 4, np.uint16), ((7, 5, 3), 8, np.uint8)])
+def test_maxgrid_is_windowed_max(orc, shape, cell, dtype):
+    from scipy.ndimage import maximum_filter
+    rng = np.random.default_rng(sum(shape))
+    level = rng.integers(0, 4096 if dtype == np.uint16 else 256, size=shape).astype(dtype)
+    g = orc.maxgrid(level, cell)
+    # window [c*cell, c*cell + cell]: a (cell+1)-wide maximum anchored at the cell's first voxel
+    mf = maximum_filter(level, size=cell + 1, mode="nearest", origin=-(cell // 2))
+    ref = mf[::cell, ::cell, ::cell]
+    assert np.array_equal(g, ref)
