@@ -44,6 +44,12 @@ def workload(name: str):
         return dict(spec=spec, bits=12, nbins=4096, level0=(512, 512, 512), nlevels=3, nviews=36, size=1024,
                     az_step=10.0, desc="mid (profiling): u16 12-bit 1008x1008x900 phantom (1.8 GB), 4096 bins, "
                                        "Otsu, levels 512^3/256^3/128^3, 36-view turntable 1024x1024, step 0.5")
+    if name == "slab":
+        spec = phantom.VolumeSpec(2016, 2016, 224, bits=12, seed=1002, n_ell=12, n_cyl=300)
+        return dict(spec=spec, bits=12, nbins=4096, level0=(512, 512, 64), nlevels=3, nviews=4, size=1024,
+                    az_step=10.0, desc="slab (profiling): u16 12-bit 2016x2016x224 phantom (1.8 GB) with the full "
+                                       "workload's footprints, 4096 bins, Otsu, levels 512x512x64/256x256x32/"
+                                       "128x128x16, 4 views 1024x1024")
     spec = phantom.SMALL
     return dict(spec=spec, bits=8, nbins=256, level0=(128, 128, 128), nlevels=1, nviews=1, size=256,
                 az_step=0.0, desc="small: u8 256^3 phantom, 256 bins, Otsu, level 128^3, 1 view 256x256")
@@ -365,7 +371,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "mid", "small"])
+    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = workload(args.workload)

@@ -167,7 +167,7 @@ class Slicemap:
 
 def build_slicemap(vol: torch.Tensor, bits: int, sm: Slicemap, keep: torch.Tensor | None = None,
                    stream=None) -> Slicemap:
-    """Fill sm's atlases from vol (keep table applied first when given)."""
+    """Fill sm's atlases (and max grids) from vol, keep table applied first when given."""
     _cuda(vol, "vol")
     d = volume_desc(vol, bits)
     s = sm.desc()

@@ -16,13 +16,14 @@
 //    shared memory, premultiplied over-compositing, exit once A >= alpha_stop.
 //
 // Empty-space skipping: when the level has a max grid, every CTA turns it
-// into a shared-memory bitmap of the 8^3 cells that can produce a nonzero
-// opacity under this call's transfer function.  A sample whose lower corner
-// lies in an unmarked cell has opacity exactly 0 (all its corners are at or
-// below a value whose lookup lands on zero-opacity entries, evaluated with the
-// same FP32 operations as a full sample), so it adds exactly nothing to C and
-// A and is not evaluated; images and sample counts equal those of a full
-// march.
+// into a shared-memory bitmap of the 8^3 cells whose maximum (over the cell
+// plus one voxel, i.e. every voxel a sample with its lower corner in the cell
+// reads) can produce a nonzero opacity under this call's transfer function.
+// A sample whose lower corner lies in an unmarked cell has opacity exactly 0
+// (all its corners are at or below a value whose lookup lands on zero-opacity
+// entries, evaluated with the same FP32 operations as a full sample), so it
+// adds exactly nothing to C and A and is not evaluated; images and sample
+// counts equal those of a full march.
 //
 // CTAs are persistent (one wave sized by occupancy) and walk the 16 x 16 pixel
 // tiles of all views in order; a warp covers an 8 x 4 pixel sub-tile so its
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
     unsigned long long taken_total = 0;
     int v = 0, cur_level = -1;
     bool use_skip = false;
-    int gx = 0, gy = 0;
+    int gx = 0, gy = 0, wpr = 1;
 
     for (int64_t tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
         while (v + 1 < P.nviews && tile >= P.view[v + 1].tile_begin) ++v;
@@ -148,17 +149,20 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
                 const int row = z / Lv.tiles_x, col = z - row * Lv.tiles_x;
                 slice_off[z] = uint32_t(int64_t(row) * Lv.my * Lv.pitch + int64_t(col) * Lv.mx);
             }
-            const int64_t ncells = int64_t(Lv.gx) * Lv.gy * Lv.gz;
-            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && ncells <= 32 * kMaxBitmapWords;
+            // occupancy bitmap, one bit per cell, rows of wpr words per (cz, cy)
+            wpr = (Lv.gx + 31) / 32;
+            const int nrows = Lv.gy * Lv.gz;
+            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && int64_t(nrows) * wpr <= kMaxBitmapWords;
             gx = Lv.gx;
             gy = Lv.gy;
             if (use_skip) {
-                const int nwords = int((ncells + 31) / 32);
-                for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+                // exact bits: a cell is marked when its maximum exceeds S
+                for (int w = threadIdx.x; w < nrows * wpr; w += blockDim.x) {
+                    const int r = w / wpr, wx = w - r * wpr;
                     uint32_t bits = 0;
                     for (int b = 0; b < 32; ++b) {
-                        const int64_t c = int64_t(w) * 32 + b;
-                        if (c < ncells && int(__ldg(Lv.maxgrid + c)) > skip_S) bits |= 1u << b;
+                        const int cx = wx * 32 + b;
+                        if (cx < Lv.gx && int(__ldg(Lv.maxgrid + int64_t(r) * Lv.gx + cx)) > skip_S) bits |= 1u << b;
                     }
                     occ[w] = bits;
                 }
@@ -220,8 +224,9 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
                 const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
                 const int x0 = min(max(ix, 0), Mm1x), y0i = min(max(iy, 0), Mm1y), z0i = min(max(iz, 0), Mm1z);
                 if (use_skip) {
-                    const int cell = ((z0i >> 3) * gy + (y0i >> 3)) * gx + (x0 >> 3);
-                    if (!((occ[cell >> 5] >> (cell & 31)) & 1u)) {
+                    const int cx = x0 >> 3;
+                    const uint32_t word = occ[((z0i >> 3) * gy + (y0i >> 3)) * wpr + (cx >> 5)];
+                    if (!((word >> (cx & 31)) & 1u)) {
                         ++k;
 #pragma unroll
                         for (int a = 0; a < 3; ++a) U[a] += dU[a];

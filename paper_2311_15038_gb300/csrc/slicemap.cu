@@ -17,12 +17,15 @@
 //    memory, divide, write the level-0 atlas row and keep the value in shared
 //    memory;
 //  * after the group: levels 1..f from shared memory.
-// Remaining levels (f < nlevels - 1) run as a separate 2x2x2 kernel.
+// Loads are plain 16-byte streaming loads, 8 in flight per thread, 4 CTAs per
+// SM.  For a step keep table on data of at most 15 bits two 16-bit values are
+// tested and added per 32-bit word (see add_vector).  Remaining levels run as a
+// separate 2x2x2 kernel, and max grids are built by maxgrid_kernel.
 // When the keep table is a step (keep[b] = b >= T, as Otsu, ITS and explicit
 // thresholds produce) the per-voxel table lookup becomes one comparison.
 #include <algorithm>
 
-#include "mctp_internal.cuh"
+#include "slicemap_common.cuh"
 
 namespace mctp {
 namespace {
@@ -44,45 +47,32 @@ struct L0Args {
     int32_t nbins;
     int32_t shift;
     uint32_t limit;             // 2^bits
+    int32_t packed;             // two-lane u16 arithmetic is exact for this volume
 };
 
-// Keep/discard of one grey value: 0 = no table, 1 = table lookup, 2 = step.
-template <int kMode>
-__device__ __forceinline__ uint32_t kept(uint32_t v, const uint8_t *lut, int shift, uint32_t limit,
-                                         uint32_t lo)
-{
-    if (kMode == 0) return v;
-    if (kMode == 2) return (v - lo) < (limit - lo) ? v : 0u;
-    return (v < limit && lut[v >> shift]) ? v : 0u;
-}
-
-template <typename T>
-__device__ __forceinline__ T *atlas_ptr(T *atlas, int64_t pitch, int tiles_x, int m_x, int m_y, int x, int y,
-                                        int z)
-{
-    const int row = z / tiles_x, col = z - (z / tiles_x) * tiles_x;
-    return atlas + (int64_t(row) * m_y + y) * pitch + int64_t(col) * m_x + x;
-}
-
-// Column sums of one level-0 row, vector path (rows 16-byte aligned).
-template <typename T, int kMode>
-__device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int64_t zlo, int64_t zhi, int64_t ylo,
-                                                   int64_t yhi, uint32_t *colsum, const uint8_t *lut,
-                                                   uint32_t lo)
+// Column sums of one level-0 row, vector path (rows 16-byte aligned): each
+// thread owns 16-byte column vectors and sums them over the footprint's
+// source rows in registers, 8 loads in flight.
+template <typename T, int kMode, bool kPacked>
+__device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int zlo, int zhi, int ylo, int yhi,
+                                                   uint32_t *colsum, const uint8_t *lut, uint32_t lo)
 {
     constexpr int E = 16 / sizeof(T);
+    constexpr int NA = kPacked ? 4 : E;
     const int64_t V = a.nx / E;
-    const int wy = int(yhi - ylo);
-    const int R = int(zhi - zlo) * wy;
+    const int wy = yhi - ylo;
+    const int R = (zhi - zlo) * wy;
     const int64_t row_bytes = a.nx * int64_t(sizeof(T));
     // source rows of the footprint in (z, y) order: step one row, or jump to
     // the first footprint row of the next slice
     const int64_t slice_jump = (a.ny - wy + 1) * row_bytes;
-    const char *first = reinterpret_cast<const char *>(a.vol) + (zlo * a.ny + ylo) * row_bytes;
+    const char *first = reinterpret_cast<const char *>(a.vol) + (int64_t(zlo) * a.ny + ylo) * row_bytes;
+    const uint32_t k_fast = (0x8000u - lo) * 0x00010001u, ovf_bits = ~((a.limit - 1u) * 0x00010001u);
     for (int64_t v = threadIdx.x; v < V; v += blockDim.x) {
-        uint32_t sum[E];
+        uint32_t acc[NA];
 #pragma unroll
-        for (int e = 0; e < E; ++e) sum[e] = 0u;
+        for (int e = 0; e < NA; ++e) acc[e] = 0u;
+        uint32_t seen = 0;
         const char *p = first + v * 16;
         int yi = 0;
         for (int r0 = 0; r0 < R; r0 += kSmUnroll) {
@@ -98,32 +88,38 @@ __device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int64_t z
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kSmUnroll; ++u) {
-                const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+            for (int u = 0; u < kSmUnroll; ++u)
+                add_vector<T, kMode, kPacked>(q[u], acc, lut, a.shift, a.limit, lo, k_fast, seen);
+        }
+        if (kPacked && kMode == 2 && (seen & ovf_bits)) {
+            // a value at or above 2^bits: redo this vector with the exact test
+            const uint32_t k_lo2 = lo * 0x00010001u, k_lim2 = a.limit * 0x00010001u;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (sizeof(T) == 1) {
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            sum[4 * k + b] += kept<kMode>((w[k] >> (8 * b)) & 0xffu, lut, a.shift, a.limit, lo);
-                    } else {
-                        sum[2 * k] += kept<kMode>(w[k] & 0xffffu, lut, a.shift, a.limit, lo);
-                        sum[2 * k + 1] += kept<kMode>(w[k] >> 16, lut, a.shift, a.limit, lo);
-                    }
-                }
+            for (int e = 0; e < NA; ++e) acc[e] = 0u;
+            p = first + v * 16;
+            yi = 0;
+            for (int r = 0; r < R; ++r) {
+                add_vector_exact(ld_stream_v4(p), acc, k_lo2, k_lim2);
+                if (++yi == wy) { yi = 0; p += slice_jump; }
+                else p += row_bytes;
             }
         }
         uint32_t *dst = colsum + v * E;
+        if (kPacked) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(acc[0] & 0xffffu, acc[0] >> 16, acc[1] & 0xffffu, acc[1] >> 16);
+            *reinterpret_cast<uint4 *>(dst + 4) =
+                make_uint4(acc[2] & 0xffffu, acc[2] >> 16, acc[3] & 0xffffu, acc[3] >> 16);
+        } else {
 #pragma unroll
-        for (int e = 0; e < E; e += 4) *reinterpret_cast<uint4 *>(dst + e) = make_uint4(sum[e], sum[e + 1], sum[e + 2], sum[e + 3]);
+            for (int e = 0; e < E; e += 4) *reinterpret_cast<uint4 *>(dst + e) = make_uint4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+        }
     }
 }
 
 // Column sums of one level-0 row, scalar path (any alignment).
 template <typename T, int kMode>
-__device__ __forceinline__ void accumulate_row_scalar(const L0Args<T> &a, int64_t zlo, int64_t zhi, int64_t ylo,
-                                                      int64_t yhi, uint32_t *colsum, const uint8_t *lut,
-                                                      uint32_t lo)
+__device__ __forceinline__ void accumulate_row_scalar(const L0Args<T> &a, int zlo, int zhi, int ylo, int yhi,
+                                                      uint32_t *colsum, const uint8_t *lut, uint32_t lo)
 {
     for (int64_t x = threadIdx.x; x < a.nx; x += blockDim.x) {
         uint32_t s = 0;
@@ -134,29 +130,29 @@ __device__ __forceinline__ void accumulate_row_scalar(const L0Args<T> &a, int64_
     }
 }
 
-template <typename T, bool kVec, int kMode>
-__device__ void level0_group(const L0Args<T> &a, int Z0, int Y0, int gz, int gy, uint32_t *colsum, uint32_t *grp,
-                             const uint8_t *lut, uint32_t lo)
+template <typename T, bool kVec, int kMode, bool kPacked>
+__device__ void level0_group(const L0Args<T> &a, int Z0, int Y0, int gz, int gy, uint32_t *colsum, uint16_t *grp,
+                             const int32_t *zb, const int32_t *yb, const int32_t *xb, const uint8_t *lut,
+                             uint32_t lo)
 {
     const int G = gz * gy;
     for (int g = 0; g < G; ++g) {
-        const int zo = Z0 + g / gy, yo = Y0 + g % gy;
-        const int64_t zlo = (int64_t(zo) * a.nz) / a.mz, zhi = (int64_t(zo + 1) * a.nz) / a.mz;
-        const int64_t ylo = (int64_t(yo) * a.ny) / a.my, yhi = (int64_t(yo + 1) * a.ny) / a.my;
+        const int zz = g / gy, yy = g % gy;
+        const int zlo = zb[zz], zhi = zb[zz + 1], ylo = yb[yy], yhi = yb[yy + 1];
         uint32_t *cs = colsum + (g & 1) * a.nx;
-        if (kVec) accumulate_row_vec<T, kMode>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
+        if (kVec) accumulate_row_vec<T, kMode, kPacked>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
         else accumulate_row_scalar<T, kMode>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
         __syncthreads();
         const uint32_t R = uint32_t((zhi - zlo) * (yhi - ylo));
-        T *row = atlas_ptr(a.atlas[0], a.pitch[0], a.tiles_x[0], a.mx, a.my, 0, yo, zo);
+        T *row = atlas_ptr(a.atlas[0], a.pitch[0], a.tiles_x[0], a.mx, a.my, 0, Y0 + yy, Z0 + zz);
         for (int x = threadIdx.x; x < a.mx; x += blockDim.x) {
-            const int64_t xlo = (int64_t(x) * a.nx) / a.mx, xhi = (int64_t(x + 1) * a.nx) / a.mx;
+            const int xlo = xb[x], xhi = xb[x + 1];
             uint32_t s = 0;
-            for (int64_t i = xlo; i < xhi; ++i) s += cs[i];
+            for (int i = xlo; i < xhi; ++i) s += cs[i];
             const uint32_t cnt = uint32_t(xhi - xlo) * R;
             const uint32_t val = (s + cnt / 2u) / cnt;
             row[x] = (T)val;
-            if (grp) grp[g * a.mx + x] = val;
+            if (grp) grp[g * a.mx + x] = uint16_t(val);
         }
         // no barrier: the next row accumulates into the other buffer, and the
         // barrier after it orders this row's reads before that buffer's reuse
@@ -164,43 +160,35 @@ __device__ void level0_group(const L0Args<T> &a, int Z0, int Y0, int gz, int gy,
 }
 
 template <typename T, bool kVec>
-__global__ void __launch_bounds__(kSmThreads) slicemap_level0_kernel(L0Args<T> a)
+__global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T> a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int gz = 1 << a.fused, gy = 1 << a.fused;
     const int ngy = a.my / gy;
     const int Z0 = (blockIdx.x / ngy) * gz, Y0 = (blockIdx.x % ngy) * gy;
 
-    uint32_t *colsum = reinterpret_cast<uint32_t *>(smem);              // 2 * nx
-    uint32_t *grp = colsum + 2 * a.nx;                                   // gz*gy*mx (when fused)
-    uint32_t *grp1 = grp + (a.fused ? gz * gy * a.mx : 0);              // (gz/2)(gy/2)(mx/2)
+    uint32_t *colsum = reinterpret_cast<uint32_t *>(smem);                     // 2 * nx
+    int32_t *xb = reinterpret_cast<int32_t *>(colsum + 2 * a.nx);              // mx + 1
+    int32_t *zb = xb + a.mx + 1;                                               // gz + 1 (this group)
+    int32_t *yb = zb + gz + 1;                                                 // gy + 1
+    uint16_t *grp = reinterpret_cast<uint16_t *>(yb + gy + 1);                 // gz*gy*mx (when fused)
+    uint16_t *grp1 = grp + (a.fused ? gz * gy * a.mx : 0);                     // (gz/2)(gy/2)(mx/2)
     uint8_t *lut = reinterpret_cast<uint8_t *>(grp1 + (a.fused > 1 ? (gz / 2) * (gy / 2) * (a.mx / 2) : 0));
 
-    __shared__ int sh_first, sh_violation;
-    int mode = 0;
+    for (int i = threadIdx.x; i <= a.mx; i += blockDim.x) xb[i] = int32_t((int64_t(i) * a.nx) / a.mx);
+    for (int i = threadIdx.x; i <= gz; i += blockDim.x) zb[i] = int32_t((int64_t(Z0 + i) * a.nz) / a.mz);
+    for (int i = threadIdx.x; i <= gy; i += blockDim.x) yb[i] = int32_t((int64_t(Y0 + i) * a.ny) / a.my);
+    __syncthreads();
+
+    __shared__ int sh_keep[2];
     uint32_t lo = 0;
-    if (a.keep) {
-        if (threadIdx.x == 0) { sh_first = a.nbins; sh_violation = 0; }
-        for (int b = threadIdx.x; b < a.nbins; b += blockDim.x) lut[b] = a.keep[b];
-        __syncthreads();
-        for (int b = threadIdx.x; b < a.nbins; b += blockDim.x)
-            if (lut[b]) atomicMin(&sh_first, b);
-        __syncthreads();
-        for (int b = threadIdx.x; b < a.nbins; b += blockDim.x)
-            if (b >= sh_first && !lut[b]) sh_violation = 1;
-        __syncthreads();
-        if (sh_violation) {
-            mode = 1;
-        } else {
-            mode = 2;
-            const uint64_t l = uint64_t(sh_first) << a.shift;
-            lo = l >= a.limit ? a.limit : uint32_t(l);
-        }
-    }
-    uint32_t *g0 = a.fused ? grp : nullptr;
-    if (mode == 0) level0_group<T, kVec, 0>(a, Z0, Y0, gz, gy, colsum, g0, lut, lo);
-    else if (mode == 1) level0_group<T, kVec, 1>(a, Z0, Y0, gz, gy, colsum, g0, lut, lo);
-    else level0_group<T, kVec, 2>(a, Z0, Y0, gz, gy, colsum, g0, lut, lo);
+    const int mode = load_keep_table(a.keep, a.nbins, a.shift, a.limit, lut, sh_keep, int(threadIdx.x),
+                                     int(blockDim.x), &lo, [] { __syncthreads(); });
+    uint16_t *g0 = a.fused ? grp : nullptr;
+    if (mode == 0) level0_group<T, kVec, 0, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else if (mode == 1) level0_group<T, kVec, 1, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else if (a.packed) level0_group<T, kVec, 2, true>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else level0_group<T, kVec, 2, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
     if (!a.fused) return;
     __syncthreads();
 
@@ -215,12 +203,12 @@ __global__ void __launch_bounds__(kSmThreads) slicemap_level0_kernel(L0Args<T> a
             for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
-                    const uint32_t *src = grp + ((2 * c + dz) * gy + (2 * b + dy)) * a.mx + 2 * x;
-                    s += src[0] + src[1];
+                    const uint16_t *src = grp + ((2 * c + dz) * gy + (2 * b + dy)) * a.mx + 2 * x;
+                    s += uint32_t(src[0]) + uint32_t(src[1]);
                 }
             const uint32_t val = (s + 4u) / 8u;
             *atlas_ptr(a.atlas[1], a.pitch[1], a.tiles_x[1], hx, my1, x, Y0 / 2 + b, Z0 / 2 + c) = (T)val;
-            if (a.fused > 1) grp1[(c * hy + b) * hx + x] = val;
+            if (a.fused > 1) grp1[(c * hy + b) * hx + x] = uint16_t(val);
         }
     }
     if (a.fused < 2) return;
@@ -236,8 +224,8 @@ __global__ void __launch_bounds__(kSmThreads) slicemap_level0_kernel(L0Args<T> a
             for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
-                    const uint32_t *src = grp1 + ((2 * c + dz) * gy1 + (2 * b + dy)) * mx1 + 2 * x;
-                    s += src[0] + src[1];
+                    const uint16_t *src = grp1 + ((2 * c + dz) * gy1 + (2 * b + dy)) * mx1 + 2 * x;
+                    s += uint32_t(src[0]) + uint32_t(src[1]);
                 }
             *atlas_ptr(a.atlas[2], a.pitch[2], a.tiles_x[2], hx, my2, x, Y0 / 4 + b, Z0 / 4 + c) =
                 (T)((s + 4u) / 8u);
@@ -269,24 +257,32 @@ __global__ void __launch_bounds__(256) halve_kernel(const T *__restrict__ src, i
 }
 
 // Per-cell maxima of a level (occupancy data for the renderer): cell c covers
-// voxels [8c, 8c + 8] per axis, clamped.  One block per (cz, cy) row of
-// cells: the 9 x 9 (y, z) atlas rows of the row are read coalesced and their
-// column maxima kept in shared memory, then each cell takes the maximum of
-// its 9 columns.
+// voxels [8c, 8c + 8] per axis, clamped (the cell plus the first voxel of the
+// next one: everything a trilinear sample with its lower corner in the cell
+// reads).  One block per (cz, cy) row of cells; each thread keeps column
+// maxima of its x positions over the cell rows' 9 x 9 (y, z) atlas rows,
+// loading the 9 rows of a slice together, then each cell takes the maximum of
+// its 9 columns from shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) maxgrid_kernel(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx,
                                                       int my, int mz, uint16_t *__restrict__ grid, int gx, int gy)
 {
     extern __shared__ uint32_t colmax[];
+    constexpr int c = MCTP_MAXGRID_CELL;
     const int cy = blockIdx.x % gy, cz = blockIdx.x / gy;
-    const int c = MCTP_MAXGRID_CELL;
-    for (int x = threadIdx.x; x < mx; x += blockDim.x) colmax[x] = 0u;
-    const int z1 = min(cz * c + c, mz - 1), y1 = min(cy * c + c, my - 1);
-    for (int z = cz * c; z <= z1; ++z)
-        for (int y = cy * c; y <= y1; ++y) {
-            const T *row = atlas_ptr(const_cast<T *>(atlas), pitch, tiles_x, mx, my, 0, y, z);
-            for (int x = threadIdx.x; x < mx; x += blockDim.x) colmax[x] = max(colmax[x], uint32_t(__ldg(row + x)));
+    const int z1 = min(cz * c + c, mz - 1), y0 = cy * c, ny_rows = min(cy * c + c, my - 1) - y0 + 1;
+    for (int x = threadIdx.x; x < mx; x += blockDim.x) {
+        uint32_t m = 0;
+        for (int z = cz * c; z <= z1; ++z) {
+            const T *row = atlas_ptr(const_cast<T *>(atlas), pitch, tiles_x, mx, my, x, y0, z);
+            uint32_t v[c + 1];
+#pragma unroll
+            for (int r = 0; r <= c; ++r) v[r] = r < ny_rows ? uint32_t(__ldg(row + int64_t(r) * pitch)) : 0u;
+#pragma unroll
+            for (int r = 0; r <= c; ++r) m = max(m, v[r]);
         }
+        colmax[x] = m;
+    }
     __syncthreads();
     for (int cx = threadIdx.x; cx < gx; cx += blockDim.x) {
         uint32_t m = 0;
@@ -314,41 +310,66 @@ int zero_unused_tiles(void *atlas, int esize, int mx, int my, int mz, int tx, in
 }
 
 template <typename T>
+int launch_maxgrid(const mctp_slicemap *sm, int k, cudaStream_t s)
+{
+    const int c = MCTP_MAXGRID_CELL;
+    const int mx = sm->dims[k][0], my = sm->dims[k][1], mz = sm->dims[k][2];
+    const int gx = (mx + c - 1) / c, gy = (my + c - 1) / c, gz = (mz + c - 1) / c;
+    const size_t smem = size_t(mx) * sizeof(uint32_t);
+    if (smem > 200 * 1024) return MCTP_EUNSUPPORTED;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(maxgrid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return MCTP_ECUDA;
+    maxgrid_kernel<T><<<unsigned(int64_t(gy) * gz), 256, smem, s>>>(
+        static_cast<const T *>(sm->atlas[k]), int64_t(sm->tiles_x[k]) * mx, sm->tiles_x[k], mx, my, mz,
+        static_cast<uint16_t *>(sm->maxgrid[k]), gx, gy);
+    return launch_status();
+}
+
+template <typename T>
 int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep, int nbins, const mctp_slicemap *sm,
                     cudaStream_t s)
 {
-    const int fused = std::min(sm->nlevels - 1, kMaxFused);
-    L0Args<T> a{};
-    a.vol = vol;
-    a.nx = d->nx; a.ny = d->ny; a.nz = d->nz;
-    a.mx = sm->dims[0][0]; a.my = sm->dims[0][1]; a.mz = sm->dims[0][2];
-    a.fused = fused;
-    for (int k = 0; k <= fused; ++k) {
-        a.atlas[k] = static_cast<T *>(sm->atlas[k]);
-        a.tiles_x[k] = sm->tiles_x[k];
-        a.pitch[k] = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
+    int rc = MCTP_OK;
+    int done_levels = 0;   // levels 1..done_levels written by the level-0 kernel
+    {
+        const int fused = std::min(sm->nlevels - 1, kMaxFused);
+        L0Args<T> a{};
+        a.vol = vol;
+        a.nx = d->nx; a.ny = d->ny; a.nz = d->nz;
+        a.mx = sm->dims[0][0]; a.my = sm->dims[0][1]; a.mz = sm->dims[0][2];
+        a.fused = fused;
+        for (int k = 0; k <= fused; ++k) {
+            a.atlas[k] = static_cast<T *>(sm->atlas[k]);
+            a.tiles_x[k] = sm->tiles_x[k];
+            a.pitch[k] = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
+        }
+        a.keep = keep;
+        a.nbins = keep ? nbins : 0;
+        a.shift = keep ? bin_shift(d->bits, nbins) : 0;
+        a.limit = 1u << d->bits;
+        const int gz = 1 << fused, gy = 1 << fused;
+        // two 16-bit lanes per word stay exact when a footprint's sum fits 16 bits
+        const int64_t rmax = ((d->ny + a.my - 1) / a.my) * ((d->nz + a.mz - 1) / a.mz);
+        a.packed = sizeof(T) == 2 && d->bits <= 15 && rmax * ((int64_t(1) << d->bits) - 1) < 65536;
+        size_t smem = size_t(2) * a.nx * 4 + size_t(a.mx + 1 + gz + 1 + gy + 1) * 4;
+        if (fused) smem += size_t(gz) * gy * a.mx * 2;
+        if (fused > 1) smem += size_t(gz / 2) * (gy / 2) * (a.mx / 2) * 2;
+        smem += keep ? size_t(nbins) : 0;
+        if (smem > 220 * 1024) return MCTP_EUNSUPPORTED;
+        const bool vec = (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && ((a.nx * int64_t(sizeof(T))) & 15) == 0;
+        auto kern = vec ? slicemap_level0_kernel<T, true> : slicemap_level0_kernel<T, false>;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+            return MCTP_ECUDA;
+        const int64_t blocks = int64_t(a.mz / gz) * (a.my / gy);
+        if (blocks > 0x7fffffff) return MCTP_EUNSUPPORTED;
+        kern<<<unsigned(blocks), kSmThreads, smem, s>>>(a);
+        rc = launch_status();
+        if (rc != MCTP_OK) return rc;
+        done_levels = fused;
     }
-    a.keep = keep;
-    a.nbins = keep ? nbins : 0;
-    a.shift = keep ? bin_shift(d->bits, nbins) : 0;
-    a.limit = d->bits >= 32 ? 0xffffffffu : (1u << d->bits);
-    const int gz = 1 << fused, gy = 1 << fused;
-    size_t smem = size_t(2) * a.nx * 4;
-    if (fused) smem += size_t(gz) * gy * a.mx * 4;
-    if (fused > 1) smem += size_t(gz / 2) * (gy / 2) * (a.mx / 2) * 4;
-    smem += keep ? size_t(nbins) : 0;
-    if (smem > 220 * 1024) return MCTP_EUNSUPPORTED;
-    const bool vec = (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && ((a.nx * int64_t(sizeof(T))) & 15) == 0;
-    auto kern = vec ? slicemap_level0_kernel<T, true> : slicemap_level0_kernel<T, false>;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-        return MCTP_ECUDA;
-    const int64_t blocks = int64_t(a.mz / gz) * (a.my / gy);
-    if (blocks > 0x7fffffff) return MCTP_EUNSUPPORTED;
-    kern<<<unsigned(blocks), kSmThreads, smem, s>>>(a);
-    int rc = launch_status();
-    if (rc != MCTP_OK) return rc;
-    for (int k = fused + 1; k < sm->nlevels; ++k) {
+    for (int k = done_levels + 1; k < sm->nlevels; ++k) {
         const int mx = sm->dims[k - 1][0], my = sm->dims[k - 1][1];
         const int64_t total = int64_t(sm->dims[k][0]) * sm->dims[k][1] * sm->dims[k][2];
         const int64_t grid = std::min<int64_t>((total + 255) / 256, int64_t(num_sms()) * 16);
@@ -365,18 +386,7 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
     }
     for (int k = 0; k < sm->nlevels; ++k) {
         if (!sm->maxgrid[k]) continue;
-        const int c = MCTP_MAXGRID_CELL;
-        const int mx = sm->dims[k][0], my = sm->dims[k][1], mz = sm->dims[k][2];
-        const int gx = (mx + c - 1) / c, gy = (my + c - 1) / c, gz = (mz + c - 1) / c;
-        const size_t smem = size_t(mx) * sizeof(uint32_t);
-        if (smem > 200 * 1024) return MCTP_EUNSUPPORTED;
-        if (smem > 48 * 1024 && cudaFuncSetAttribute(maxgrid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     int(smem)) != cudaSuccess)
-            return MCTP_ECUDA;
-        maxgrid_kernel<T><<<unsigned(int64_t(gy) * gz), 256, smem, s>>>(
-            static_cast<const T *>(sm->atlas[k]), int64_t(sm->tiles_x[k]) * mx, sm->tiles_x[k], mx, my, mz,
-            static_cast<uint16_t *>(sm->maxgrid[k]), gx, gy);
-        rc = launch_status();
+        rc = launch_maxgrid<T>(sm, k, s);
         if (rc != MCTP_OK) return rc;
     }
     return MCTP_OK;

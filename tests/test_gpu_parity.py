@@ -208,6 +208,21 @@ def test_slicemap(env, case):
     _check_atlases(sm, levels, oracle)
 
 
+@pytest.mark.parametrize("T", [0, 1456, 4096])
+def test_slicemap_packed_path_with_out_of_depth_values(env, T):
+    # 12-bit volume holding values up to 65535: the step keep table must drop
+    # every value >= 4096 (and >= 32768) exactly on the two-lane path
+    mctp, oracle, phantom, dev = env
+    rng = np.random.default_rng(T)
+    vol = rng.integers(0, 65536, size=(64, 48, 40)).astype(np.uint16)
+    vol[::3] = rng.integers(0, 4096, size=vol[::3].shape)
+    keep_ref = oracle.keep_threshold(4096, T)
+    dims = [(16, 16, 16), (8, 8, 8)]
+    sm = mctp.Slicemap.allocate((40, 48, 64), dims[0], 2, torch.uint16, 12, dev)
+    mctp.build_slicemap(up(vol, dev), 12, sm, up(keep_ref, dev))
+    _check_atlases(sm, oracle.slicemap(vol, 12, dims, keep_ref), oracle)
+
+
 def test_slicemap_custom_tiles(env):
     mctp, oracle, phantom, dev = env
     vol = phantom.generate_cpu(phantom.VolumeSpec(64, 48, 52, bits=8, seed=12, n_ell=4))
