@@ -22,8 +22,10 @@
 // A sample whose lower corner lies in an unmarked cell has opacity exactly 0
 // (all its corners are at or below a value whose lookup lands on zero-opacity
 // entries, evaluated with the same FP32 operations as a full sample), so it
-// adds exactly nothing to C and A and is not evaluated; images and sample
-// counts equal those of a full march.
+// adds exactly nothing to C and A and is not evaluated: an exact integer DDA
+// over the cells gives the index of the first sample of the next cell, and the
+// march jumps there at once.  Images and sample counts equal those of a full
+// march.
 //
 // CTAs are persistent (one wave sized by occupancy) and walk the 16 x 16 pixel
 // tiles of all views in order; a warp covers an 8 x 4 pixel sub-tile so its
@@ -118,7 +120,7 @@ __device__ int skip_threshold(const float4 *lut, int nlut, float inv_vmax, int v
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_constant__ RenderParams P)
+__global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_constant__ RenderParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     float4 *lut = reinterpret_cast<float4 *>(smem);
@@ -205,39 +207,83 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
         if (n > 0) {
             // ---- fixed-point level coordinates of sample 0 and the step
             const double t0 = double(tmin) + 0.5 * double(V.delta);
-            long long U[3], dU[3];
+            long long U0[3], dU[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double q0 = (double(o[a]) + t0 * double(d[a])) * V.scale[a] - 0.5;
                 const double dq = double(V.delta) * double(d[a]) * V.scale[a];
-                U[a] = __double2ll_rn(q0 * 4294967296.0);
+                U0[a] = __double2ll_rn(q0 * 4294967296.0);
                 dU[a] = __double2ll_rn(dq * 4294967296.0);
             }
-            const int Mm1x = Lv.mx - 1, Mm1y = Lv.my - 1, Mm1z = Lv.mz - 1;
+            const int Mm1[3] = {Lv.mx - 1, Lv.my - 1, Lv.mz - 1};
+            // ---- exact integer DDA over the 8^3 cells of each sample's lower
+            // corner: nxt[a] is the first sample index whose corner is in the
+            // next cell along axis a; with m = |dU|, D = 8 voxels, D = q m + r,
+            // the crossing after one at c (slack e = c m - distance) is at
+            // c + q + (r > e), slack e + (r > e ? m : 0) - r
+            constexpr long long kInf = 0x7fffffffffffffffLL;
+            constexpr long long kD = 8LL << 32;
+            int cc[3];
+            long long nxt[3], ee[3], qq[3], rr[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                cc[a] = min(max(int(U0[a] >> 32), 0), Mm1[a]) >> 3;
+                nxt[a] = kInf;
+                ee[a] = qq[a] = rr[a] = 0;
+                const int last = Mm1[a] >> 3;
+                if (use_skip && dU[a] != 0 && (dU[a] > 0 ? cc[a] < last : cc[a] > 0)) {
+                    const long long m = dU[a] > 0 ? dU[a] : -dU[a];
+                    const long long num = dU[a] > 0 ? ((long long)(8 * cc[a] + 8) << 32) - U0[a]
+                                                    : U0[a] - ((long long)(8 * cc[a]) << 32) + 1;
+                    const long long c = (num + m - 1) / m;
+                    nxt[a] = c;
+                    ee[a] = c * m - num;
+                    qq[a] = kD / m;
+                    rr[a] = kD - qq[a] * m;
+                }
+            }
+            auto cross = [&](int a) {
+                cc[a] += dU[a] > 0 ? 1 : -1;
+                if (dU[a] > 0 ? cc[a] >= (Mm1[a] >> 3) : cc[a] <= 0) {
+                    nxt[a] = kInf;  // the last cell this way: clamping keeps the corner in it
+                    return;
+                }
+                const long long m = dU[a] > 0 ? dU[a] : -dU[a];
+                const bool up = rr[a] > ee[a];
+                nxt[a] += qq[a] + (up ? 1 : 0);
+                ee[a] += (up ? m : 0) - rr[a];
+            };
             const T *atlas = static_cast<const T *>(Lv.atlas);
             const uint32_t pitch = uint32_t(Lv.pitch);
             const float nl1 = float(P.nlut - 1);
             const int jmax = P.nlut - 2;
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-            int64_t k = 0;
+            long long k = 0;
             while (k < n) {
-                const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
-                const int x0 = min(max(ix, 0), Mm1x), y0i = min(max(iy, 0), Mm1y), z0i = min(max(iz, 0), Mm1z);
                 if (use_skip) {
-                    const int cx = x0 >> 3;
-                    const uint32_t word = occ[((z0i >> 3) * gy + (y0i >> 3)) * wpr + (cx >> 5)];
-                    if (!((word >> (cx & 31)) & 1u)) {
-                        ++k;
+                    const uint32_t word = occ[(cc[2] * gy + cc[1]) * wpr + (cc[0] >> 5)];
+                    if (!((word >> (cc[0] & 31)) & 1u)) {
+                        // an empty cell: its samples have opacity exactly 0; jump
+                        // to the first sample of the next cell
+                        const long long kn = min(min(nxt[0], nxt[1]), nxt[2]);
+                        if (kn >= n) { k = n; break; }
+                        k = kn;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) U[a] += dU[a];
+                        for (int a = 0; a < 3; ++a)
+                            if (nxt[a] == kn) cross(a);
                         continue;
                     }
                 }
+                long long U[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) U[a] = U0[a] + k * dU[a];
+                const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
+                const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]), z0i = min(max(iz, 0), Mm1[2]);
+                const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
+                const int z1i = min(max(iz + 1, 0), Mm1[2]);
                 const float fx = float(uint32_t(U[0])) * 2.3283064365386963e-10f;
                 const float fy = float(uint32_t(U[1])) * 2.3283064365386963e-10f;
                 const float fz = float(uint32_t(U[2])) * 2.3283064365386963e-10f;
-                const int x1 = min(max(ix + 1, 0), Mm1x), y1i = min(max(iy + 1, 0), Mm1y);
-                const int z1i = min(max(iz + 1, 0), Mm1z);
                 const uint32_t za = slice_off[z0i], zb = slice_off[z1i];
                 const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
                 const float v000 = texel(atlas, za + ya + x0), v100 = texel(atlas, za + ya + x1);
@@ -259,8 +305,11 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
                 A += w;
                 ++k;
                 if (A >= P.alpha_stop) break;
+                if (use_skip) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) U[a] += dU[a];
+                    for (int a = 0; a < 3; ++a)
+                        if (nxt[a] == k) cross(a);
+                }
             }
             acc = make_float4(C0, C1, C2, A);
             taken_total += (unsigned long long)k;
