@@ -7,10 +7,12 @@
 //  * set-up in FP32 with one rounding per operation in a fixed order (camera
 //    origin, slab intersection, sample count n = floor((t_far - t_near) /
 //    Delta)), so n matches any other IEEE implementation of the same steps;
-//  * the level coordinate of sample k is q0 + k dq; q0 and dq are formed in
-//    FP64 once per ray and held as 32.32 fixed-point integers, so stepping is
-//    an exact integer add and the sample position is accurate to ~1e-9 voxel
-//    (an FP32 position would carry ~3e-5 voxel of rounding at 512 voxels);
+//  * the level coordinate of sample k is q0 + k dq, held as 32.32 fixed-point
+//    integers: dq once per view on the host (FP64), q0 once per ray in
+//    float-float arithmetic (no FP64, which runs at a small fraction of the
+//    FP32 rate on this part), so stepping is exact integer arithmetic and a
+//    sample position is accurate to ~1e-9 voxel (an FP32 position would carry
+//    ~3e-5 voxel of rounding at 512 voxels);
 //  * trilinear interpolation of the atlas in FP32 (corner indices clamped to
 //    the level), transfer-function lookup with linear interpolation from
 //    shared memory, premultiplied over-compositing, exit once A >= alpha_stop.
@@ -55,7 +57,11 @@ struct ViewParams {
     int32_t W, H;
     int32_t tiles_w;  // image tiles along x
     int32_t level;
-    double scale[3];  // level voxels per world unit, M_a / N_a
+    float sc_hi[3], sc_lo[3];  // M_a / N_a as an unevaluated float sum
+    float inv_m[3];            // 1 / |dU| (0 when dU == 0)
+    long long dU[3];           // fixed-point step of the level coordinate per sample
+    uint32_t qq[3], rr[3];     // 8 voxels (fixed point) = qq |dU| + rr (qq capped at 2^30)
+    int32_t skip_ok;           // |dU| < 2^32 on every axis: the cell DDA runs in 32 bits
     int64_t out_offset;  // in floats
     int64_t tile_begin;  // first tile of this view
 };
@@ -89,6 +95,38 @@ template <typename T>
 __device__ __forceinline__ float texel(const T *atlas, uint32_t off)
 {
     return float(__ldg(atlas + off));
+}
+
+// Error-free transformations (Knuth's TwoSum; the FMA TwoProduct): a + b and
+// a * b as an unevaluated sum hi + lo of two floats.
+__device__ __forceinline__ void two_sum(float a, float b, float &hi, float &lo)
+{
+    hi = __fadd_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &hi, float &lo)
+{
+    hi = __fmul_rn(a, b);
+    lo = fmaf(a, b, -hi);
+}
+
+// Fixed-point (32.32) level coordinate (o + t0 d) * sc - 1/2 of a ray's first
+// sample, t0 = tn + h, in float-float arithmetic (relative error ~2^-44): no
+// FP64 on the per-ray path.
+__device__ __forceinline__ long long start_coord(float o, float d, float tn, float h, float sc_hi, float sc_lo)
+{
+    float t_hi, t_lo, p_hi, p_lo, s_hi, s_lo, m_hi, m_lo;
+    two_sum(tn, h, t_hi, t_lo);
+    two_prod(t_hi, d, p_hi, p_lo);
+    p_lo = fmaf(t_lo, d, p_lo);
+    two_sum(o, p_hi, s_hi, s_lo);
+    s_lo = __fadd_rn(s_lo, p_lo);
+    two_prod(s_hi, sc_hi, m_hi, m_lo);
+    m_lo = fmaf(s_hi, sc_lo, fmaf(s_lo, sc_hi, m_lo));
+    return __float2ll_rn(__fmul_rn(m_hi, 4294967296.0f)) + __float2ll_rn(__fmul_rn(m_lo, 4294967296.0f)) -
+           (1LL << 31);
 }
 
 // Lookup coordinate of a raw interpolated value, as the march computes it.
@@ -138,7 +176,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
     unsigned long long taken_total = 0;
     int v = 0, cur_level = -1;
     bool use_skip = false;
-    int gx = 0, gy = 0, wpr = 1;
+    int gy = 0, wpr = 1;
 
     for (int64_t tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
         while (v + 1 < P.nviews && tile >= P.view[v + 1].tile_begin) ++v;
@@ -154,9 +192,8 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
             // occupancy bitmap, one bit per cell, rows of wpr words per (cz, cy)
             wpr = (Lv.gx + 31) / 32;
             const int nrows = Lv.gy * Lv.gz;
-            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && int64_t(nrows) * wpr <= kMaxBitmapWords;
-            gx = Lv.gx;
             gy = Lv.gy;
+            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && int64_t(nrows) * wpr <= kMaxBitmapWords;
             if (use_skip) {
                 // exact bits: a cell is marked when its maximum exceeds S
                 for (int w = threadIdx.x; w < nrows * wpr; w += blockDim.x) {
@@ -205,68 +242,72 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
 
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (n > 0) {
-            // ---- fixed-point level coordinates of sample 0 and the step
-            const double t0 = double(tmin) + 0.5 * double(V.delta);
-            long long U0[3], dU[3];
+            // ---- fixed-point level coordinates of sample 0; the step is per view
+            long long U0[3];
+            const long long *dU = V.dU;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double q0 = (double(o[a]) + t0 * double(d[a])) * V.scale[a] - 0.5;
-                const double dq = double(V.delta) * double(d[a]) * V.scale[a];
-                U0[a] = __double2ll_rn(q0 * 4294967296.0);
-                dU[a] = __double2ll_rn(dq * 4294967296.0);
-            }
+            for (int a = 0; a < 3; ++a)
+                U0[a] = start_coord(o[a], d[a], tmin, 0.5f * V.delta, V.sc_hi[a], V.sc_lo[a]);
             const int Mm1[3] = {Lv.mx - 1, Lv.my - 1, Lv.mz - 1};
             // ---- exact integer DDA over the 8^3 cells of each sample's lower
             // corner: nxt[a] is the first sample index whose corner is in the
-            // next cell along axis a; with m = |dU|, D = 8 voxels, D = q m + r,
-            // the crossing after one at c (slack e = c m - distance) is at
-            // c + q + (r > e), slack e + (r > e ? m : 0) - r
-            constexpr long long kInf = 0x7fffffffffffffffLL;
-            constexpr long long kD = 8LL << 32;
-            int cc[3];
-            long long nxt[3], ee[3], qq[3], rr[3];
+            // next cell along axis a; with m = |dU| (< 2^32), D = 8 voxels,
+            // D = q m + r, the crossing after one at c (slack e = c m -
+            // distance, 0 <= e < m) is at c + q + (r > e), slack
+            // e + (r > e ? m : 0) - r.  Indices past the ray's end stand for
+            // "no further crossing".
+            const bool skip = use_skip && V.skip_ok;
+            constexpr int kInf = 0x7fffffff;
+            int cc[3], nxt[3];
+            uint32_t ee[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 cc[a] = min(max(int(U0[a] >> 32), 0), Mm1[a]) >> 3;
                 nxt[a] = kInf;
-                ee[a] = qq[a] = rr[a] = 0;
+                ee[a] = 0;
                 const int last = Mm1[a] >> 3;
-                if (use_skip && dU[a] != 0 && (dU[a] > 0 ? cc[a] < last : cc[a] > 0)) {
+                if (skip && dU[a] != 0 && (dU[a] > 0 ? cc[a] < last : cc[a] > 0)) {
                     const long long m = dU[a] > 0 ? dU[a] : -dU[a];
                     const long long num = dU[a] > 0 ? ((long long)(8 * cc[a] + 8) << 32) - U0[a]
                                                     : U0[a] - ((long long)(8 * cc[a]) << 32) + 1;
-                    const long long c = (num + m - 1) / m;
-                    nxt[a] = c;
-                    ee[a] = c * m - num;
-                    qq[a] = kD / m;
-                    rr[a] = kD - qq[a] * m;
+                    // c = ceil(num / m): float estimate, then exact correction
+                    const float est = float(num) * V.inv_m[a];
+                    if (est < float(n) + 2.0f) {
+                        long long c = (long long)est;
+                        while (c * m < num) ++c;
+                        while (c > 0 && (c - 1) * m >= num) --c;
+                        nxt[a] = int(c);
+                        ee[a] = uint32_t(c * m - num);
+                    }
                 }
             }
             auto cross = [&](int a) {
-                cc[a] += dU[a] > 0 ? 1 : -1;
-                if (dU[a] > 0 ? cc[a] >= (Mm1[a] >> 3) : cc[a] <= 0) {
+                const bool fwd = dU[a] > 0;
+                cc[a] += fwd ? 1 : -1;
+                if (fwd ? cc[a] >= (Mm1[a] >> 3) : cc[a] <= 0) {
                     nxt[a] = kInf;  // the last cell this way: clamping keeps the corner in it
                     return;
                 }
-                const long long m = dU[a] > 0 ? dU[a] : -dU[a];
-                const bool up = rr[a] > ee[a];
-                nxt[a] += qq[a] + (up ? 1 : 0);
-                ee[a] += (up ? m : 0) - rr[a];
+                const uint32_t m = uint32_t(fwd ? dU[a] : -dU[a]);
+                const bool up = V.rr[a] > ee[a];
+                nxt[a] = int(min(uint32_t(nxt[a]) + V.qq[a] + (up ? 1u : 0u), uint32_t(kInf)));
+                ee[a] += (up ? m : 0u) - V.rr[a];
             };
             const T *atlas = static_cast<const T *>(Lv.atlas);
             const uint32_t pitch = uint32_t(Lv.pitch);
             const float nl1 = float(P.nlut - 1);
             const int jmax = P.nlut - 2;
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-            long long k = 0;
-            while (k < n) {
-                if (use_skip) {
+            int k = 0;
+            const int nn = int(n);
+            while (k < nn) {
+                if (skip) {
                     const uint32_t word = occ[(cc[2] * gy + cc[1]) * wpr + (cc[0] >> 5)];
                     if (!((word >> (cc[0] & 31)) & 1u)) {
                         // an empty cell: its samples have opacity exactly 0; jump
                         // to the first sample of the next cell
-                        const long long kn = min(min(nxt[0], nxt[1]), nxt[2]);
-                        if (kn >= n) { k = n; break; }
+                        const int kn = min(min(nxt[0], nxt[1]), nxt[2]);
+                        if (kn >= nn) { k = nn; break; }
                         k = kn;
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
@@ -276,7 +317,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
                 }
                 long long U[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) U[a] = U0[a] + k * dU[a];
+                for (int a = 0; a < 3; ++a) U[a] = U0[a] + (long long)k * dU[a];
                 const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
                 const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]), z0i = min(max(iz, 0), Mm1[2]);
                 const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
@@ -305,7 +346,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
                 A += w;
                 ++k;
                 if (A >= P.alpha_stop) break;
-                if (use_skip) {
+                if (skip) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
                         if (nxt[a] == k) cross(a);
@@ -413,10 +454,24 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
                 V.N[a] = N[a];
                 V.c[a] = N[a] / 2.0f;
                 sa[a] = N[a] / float(M[a]);
-                V.scale[a] = double(M[a]) / double(n3[a]);
+                const double sc = double(M[a]) / double(n3[a]);
+                V.sc_hi[a] = float(sc);
+                V.sc_lo[a] = float(sc - double(V.sc_hi[a]));
             }
             const float smin = fminf(sa[0], fminf(sa[1], sa[2]));
             V.delta = w.step * smin;
+            bool ok32 = true;
+            for (int a = 0; a < 3; ++a) {
+                const double sc = double(M[a]) / double(n3[a]);
+                V.dU[a] = llrint(double(V.delta) * double(-V.b[a]) * sc * 4294967296.0);
+                const long long m = V.dU[a] < 0 ? -V.dU[a] : V.dU[a];
+                V.inv_m[a] = m ? float(1.0 / double(m)) : 0.0f;
+                const long long q = m ? (8LL << 32) / m : 0;
+                V.qq[a] = uint32_t(std::min<long long>(q, 1LL << 30));
+                V.rr[a] = uint32_t(m ? (8LL << 32) - q * m : 0);
+                if (m >= (1LL << 32)) ok32 = false;
+            }
+            V.skip_ok = ok32 ? 1 : 0;
             V.L = L;
             V.W = w.width;
             V.H = w.height;
