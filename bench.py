@@ -55,6 +55,29 @@ def workload(name: str):
                 az_step=0.0, desc="small: u8 256^3 phantom, 256 bins, Otsu, level 128^3, 1 view 256x256")
 
 
+KERNEL_SOURCES = {"histogram": "hist.cu", "slicemap": "slicemap.cu", "render": "render.cu",
+                  "threshold": "threshold.cu"}
+
+
+def measured_traffic():
+    """ncu DRAM bytes per launch (profiles/traffic.json), kept only while the
+    kernel's source file is unchanged since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    rec = json.load(open(path))
+    for kernel, src in KERNEL_SOURCES.items():
+        r = rec.get(kernel)
+        if not r:
+            continue
+        f = os.path.join(ROOT, "paper_2311_15038_gb300", "csrc", src)
+        sha = hashlib.sha256(open(f, "rb").read()).hexdigest()
+        out[kernel] = r["bytes_per_launch"] if sha == r.get("source_sha256") else None
+    return out
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -107,6 +130,15 @@ class ClockSampler:
                     reasons=reasons, samples=len(rows))
 
 
+def launches_per_step(wl, nviews):
+    """Kernels of this library launched by one step: histogram, threshold
+    selection, the level-0 slicemap kernel (levels 1-2 fused), one 2x2x2 kernel
+    per further level, one max-grid kernel per level, one render launch per 64
+    views."""
+    nl = wl["nlevels"]
+    return 1 + 1 + 1 + max(0, nl - 3) + nl + (nviews + 63) // 64
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -116,7 +148,7 @@ def dist_setup():
 
 # --------------------------------------------------------------- CPU oracle
 
-def oracle_sample(wl, slab=None):
+def oracle_sample(wl, slab=None, npix=8192):
     """Time the oracle on a bounded sample of the workload and extrapolate its
     step time.  Sample: the histogram and slicemap of a 96-slice slab around
     the middle of the volume, Otsu on that histogram, and 8192 rays of one
@@ -150,7 +182,6 @@ def oracle_sample(wl, slab=None):
     L = float(np.sqrt(float(spec.nx) ** 2 + float(spec.ny) ** 2 + float(spec.nz) ** 2))
     half_rows = max(1, int(0.5 * nz_s / (L / size)))
     rng = np.random.default_rng(0)
-    npix = 8192
     rows = rng.integers(size // 2 - half_rows, size // 2 + half_rows, size=npix)
     pix = rows * size + rng.integers(0, size, size=npix)
     t0 = time.perf_counter()
@@ -315,17 +346,18 @@ def run_gpu(args, wl):
         "threshold": dict(bound="alu", flops=0, unit="TFLOP/s"),
     }
     fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    traffic = measured_traffic() if args.workload == "full" else {}
     roof = {}
     for name, k in kernels.items():
         t = stage_ms[name] / 1e3
         if k["bound"] == "hbm":
             ach = k["bytes"] / t / 1e9
             roof[name] = dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
-                              frac=ach / pk["hbm_gbs"], ms=stage_ms[name], traffic=None)
+                              frac=ach / pk["hbm_gbs"], ms=stage_ms[name], traffic=traffic.get(name))
         else:
             ach = k["flops"] / t / 1e12
             roof[name] = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s",
-                              frac=ach / fp32_peak, ms=stage_ms[name], traffic=None)
+                              frac=ach / fp32_peak, ms=stage_ms[name], traffic=traffic.get(name))
     roof["render"]["compulsory_hbm_gbs"] = wl["nviews"] * level0_bytes / (stage_ms["render"] / 1e3) / 1e9
     dominant = max(stage_ms, key=stage_ms.get)
     steps_total = samples_per_step * args.steps * ws
@@ -345,7 +377,7 @@ def run_gpu(args, wl):
         stage_ms=stage_ms,
         roofline=dict(roof[dominant], kernel=dominant, peak_source=pk["source"]),
         roofline_by_kernel=roof,
-        gpu_launches=4 * args.steps,
+        gpu_launches=launches_per_step(wl, len(views)) * args.steps,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
         e2e=dict(value=samples_per_step / e2e_s, unit=UNIT, h2d_bytes_per_step=vol_bytes,
                  d2h_bytes_per_step=image_bytes, ms_per_step=e2e_s * 1e3),
@@ -356,7 +388,7 @@ def run_gpu(args, wl):
         nz_s = min(spec.nz, 96)
         zs = spec.nz // 2 - nz_s // 2
         del vol_host
-        step_s, samples_step, text = oracle_sample(wl, vol[zs:zs + nz_s].cpu().numpy())
+        step_s, samples_step, text = oracle_sample(wl, vol[zs:zs + nz_s].cpu().numpy(), npix=65536)
         line["cpu_baseline"] = dict(value=samples_step / step_s, unit=UNIT, cores=1, kind="oracle", sample=text)
     print(json.dumps(line), flush=True)
     if ws > 1:
