@@ -18,8 +18,10 @@
 //    memory;
 //  * after the group: levels 1..f from shared memory.
 // Loads are plain 16-byte streaming loads, 8 in flight per thread, 4 CTAs per
-// SM.  For a step keep table on data of at most 15 bits two 16-bit values are
-// tested and added per 32-bit word (see add_vector).  Remaining levels run as a
+// SM; rows that do not start on a 16-byte boundary are read as pairs of
+// aligned loads funnel-shifted together.  For a step keep table on data of at
+// most 15 bits two 16-bit values are tested and added per 32-bit word (see
+// add_vector; u8 data spreads its bytes over two such words).  Remaining levels run as a
 // separate 2x2x2 kernel, and max grids are built by maxgrid_kernel.
 // When the keep table is a step (keep[b] = b >= T, as Otsu, ITS and explicit
 // thresholds produce) the per-voxel table lookup becomes one comparison.
@@ -50,19 +52,68 @@ struct L0Args {
     int32_t packed;             // two-lane u16 arithmetic is exact for this volume
 };
 
-// Column sums of one level-0 row, vector path (rows 16-byte aligned): each
-// thread owns 16-byte column vectors and sums them over the footprint's
-// source rows in registers, 8 loads in flight.
-template <typename T, int kMode, bool kPacked>
+// 16 bytes of a source row starting at byte 16 v of the row, for any row
+// alignment: two aligned 16-byte loads funnel-shifted together.  The second
+// load is made only when its chunk holds bytes of the row (so no load leaves
+// a 16-byte chunk that holds valid data); bytes past the row end are garbage
+// and the caller ignores the elements they form.
+__device__ __forceinline__ uint4 load_row_vector(const char *row, int64_t v, int64_t row_bytes)
+{
+    const uintptr_t ad = reinterpret_cast<uintptr_t>(row) + uintptr_t(v) * 16u;
+    const uint32_t m = uint32_t(ad & 15u);
+    const char *c0 = reinterpret_cast<const char *>(ad - m);
+    const uint4 q0 = ld_stream_v4(c0);
+    if (m == 0) return q0;
+    uint4 q1 = make_uint4(0u, 0u, 0u, 0u);
+    if (c0 + 16 < row + row_bytes) q1 = ld_stream_v4(c0 + 16);
+    const uint32_t W[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    const uint32_t sh = (m & 3u) * 8u;
+    switch (m >> 2) {
+    case 0: return make_uint4(__funnelshift_r(W[0], W[1], sh), __funnelshift_r(W[1], W[2], sh),
+                              __funnelshift_r(W[2], W[3], sh), __funnelshift_r(W[3], W[4], sh));
+    case 1: return make_uint4(__funnelshift_r(W[1], W[2], sh), __funnelshift_r(W[2], W[3], sh),
+                              __funnelshift_r(W[3], W[4], sh), __funnelshift_r(W[4], W[5], sh));
+    case 2: return make_uint4(__funnelshift_r(W[2], W[3], sh), __funnelshift_r(W[3], W[4], sh),
+                              __funnelshift_r(W[4], W[5], sh), __funnelshift_r(W[5], W[6], sh));
+    default: return make_uint4(__funnelshift_r(W[3], W[4], sh), __funnelshift_r(W[4], W[5], sh),
+                               __funnelshift_r(W[5], W[6], sh), __funnelshift_r(W[6], W[7], sh));
+    }
+}
+
+// u8 data, two 16-bit lanes per word: bytes 0,2 of each word into acc[2k],
+// bytes 1,3 into acc[2k+1]; for a step table the lane test of add_vector
+// (values < 256 never carry).
+template <int kMode>
+__device__ __forceinline__ void add_vector_u8_packed(const uint4 &q, uint32_t *acc, uint32_t k_fast)
+{
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t even = w[k] & 0x00ff00ffu, odd = (w[k] >> 8) & 0x00ff00ffu;
+        if (kMode == 2) {
+            even &= lane_sign_mask(even + k_fast);
+            odd &= lane_sign_mask(odd + k_fast);
+        }
+        acc[2 * k] += even;
+        acc[2 * k + 1] += odd;
+    }
+}
+
+// Column sums of one level-0 row, vector path: each thread owns 16-byte column
+// vectors of the row and sums them over the footprint's source rows in
+// registers (aligned rows: 8 loads in flight; other rows: two loads per vector,
+// 4 rows in flight).
+template <typename T, int kMode, bool kPacked, bool kAligned>
 __device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int zlo, int zhi, int ylo, int yhi,
                                                    uint32_t *colsum, const uint8_t *lut, uint32_t lo)
 {
     constexpr int E = 16 / sizeof(T);
-    constexpr int NA = kPacked ? 4 : E;
-    const int64_t V = a.nx / E;
+    constexpr int NA = kPacked ? (sizeof(T) == 1 ? 8 : 4) : E;
+    constexpr int UNROLL = kAligned ? kSmUnroll : kSmUnroll / 2;
+    const int64_t row_bytes = a.nx * int64_t(sizeof(T));
+    const int64_t V = (row_bytes + 15) / 16;
     const int wy = yhi - ylo;
     const int R = (zhi - zlo) * wy;
-    const int64_t row_bytes = a.nx * int64_t(sizeof(T));
     // source rows of the footprint in (z, y) order: step one row, or jump to
     // the first footprint row of the next slice
     const int64_t slice_jump = (a.ny - wy + 1) * row_bytes;
@@ -73,60 +124,69 @@ __device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int zlo, 
 #pragma unroll
         for (int e = 0; e < NA; ++e) acc[e] = 0u;
         uint32_t seen = 0;
-        const char *p = first + v * 16;
+        const char *rs = first;  // start of the current source row
         int yi = 0;
-        for (int r0 = 0; r0 < R; r0 += kSmUnroll) {
-            uint4 q[kSmUnroll];
+        for (int r0 = 0; r0 < R; r0 += UNROLL) {
+            uint4 q[UNROLL];
 #pragma unroll
-            for (int u = 0; u < kSmUnroll; ++u) {
+            for (int u = 0; u < UNROLL; ++u) {
                 if (r0 + u < R) {
-                    q[u] = ld_stream_v4(p);
-                    if (++yi == wy) { yi = 0; p += slice_jump; }
-                    else p += row_bytes;
+                    q[u] = kAligned ? ld_stream_v4(rs + v * 16) : load_row_vector(rs, v, row_bytes);
+                    if (++yi == wy) { yi = 0; rs += slice_jump; }
+                    else rs += row_bytes;
                 } else {
                     q[u] = make_uint4(0u, 0u, 0u, 0u);
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kSmUnroll; ++u)
-                add_vector<T, kMode, kPacked>(q[u], acc, lut, a.shift, a.limit, lo, k_fast, seen);
+            for (int u = 0; u < UNROLL; ++u) {
+                if (kPacked && sizeof(T) == 1) add_vector_u8_packed<kMode>(q[u], acc, k_fast);
+                else add_vector<T, kMode, kPacked>(q[u], acc, lut, a.shift, a.limit, lo, k_fast, seen);
+            }
         }
-        if (kPacked && kMode == 2 && (seen & ovf_bits)) {
+        if (kPacked && sizeof(T) == 2 && kMode == 2 && (seen & ovf_bits)) {
             // a value at or above 2^bits: redo this vector with the exact test
             const uint32_t k_lo2 = lo * 0x00010001u, k_lim2 = a.limit * 0x00010001u;
 #pragma unroll
             for (int e = 0; e < NA; ++e) acc[e] = 0u;
-            p = first + v * 16;
+            rs = first;
             yi = 0;
             for (int r = 0; r < R; ++r) {
-                add_vector_exact(ld_stream_v4(p), acc, k_lo2, k_lim2);
-                if (++yi == wy) { yi = 0; p += slice_jump; }
-                else p += row_bytes;
+                add_vector_exact(kAligned ? ld_stream_v4(rs + v * 16) : load_row_vector(rs, v, row_bytes), acc,
+                                 k_lo2, k_lim2);
+                if (++yi == wy) { yi = 0; rs += slice_jump; }
+                else rs += row_bytes;
             }
         }
-        uint32_t *dst = colsum + v * E;
-        if (kPacked) {
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(acc[0] & 0xffffu, acc[0] >> 16, acc[1] & 0xffffu, acc[1] >> 16);
-            *reinterpret_cast<uint4 *>(dst + 4) =
-                make_uint4(acc[2] & 0xffffu, acc[2] >> 16, acc[3] & 0xffffu, acc[3] >> 16);
+        uint32_t sums[E];
+        if (kPacked && sizeof(T) == 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                sums[4 * k] = acc[2 * k] & 0xffffu;
+                sums[4 * k + 2] = acc[2 * k] >> 16;
+                sums[4 * k + 1] = acc[2 * k + 1] & 0xffffu;
+                sums[4 * k + 3] = acc[2 * k + 1] >> 16;
+            }
+        } else if (kPacked) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                sums[2 * k] = acc[k] & 0xffffu;
+                sums[2 * k + 1] = acc[k] >> 16;
+            }
         } else {
 #pragma unroll
-            for (int e = 0; e < E; e += 4) *reinterpret_cast<uint4 *>(dst + e) = make_uint4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+            for (int e = 0; e < E; ++e) sums[e] = acc[e];
         }
-    }
-}
-
-// Column sums of one level-0 row, scalar path (any alignment).
-template <typename T, int kMode>
-__device__ __forceinline__ void accumulate_row_scalar(const L0Args<T> &a, int zlo, int zhi, int ylo, int yhi,
-                                                      uint32_t *colsum, const uint8_t *lut, uint32_t lo)
-{
-    for (int64_t x = threadIdx.x; x < a.nx; x += blockDim.x) {
-        uint32_t s = 0;
-        for (int64_t z = zlo; z < zhi; ++z)
-            for (int64_t y = ylo; y < yhi; ++y)
-                s += kept<kMode>(__ldg(a.vol + (z * a.ny + y) * a.nx + x), lut, a.shift, a.limit, lo);
-        colsum[x] = s;
+        uint32_t *dst = colsum + v * E;
+        if (kAligned) {
+#pragma unroll
+            for (int e = 0; e < E; e += 4)
+                *reinterpret_cast<uint4 *>(dst + e) = make_uint4(sums[e], sums[e + 1], sums[e + 2], sums[e + 3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (v * E + e < a.nx) dst[e] = sums[e];
+        }
     }
 }
 
@@ -140,8 +200,7 @@ __device__ void level0_group(const L0Args<T> &a, int Z0, int Y0, int gz, int gy,
         const int zz = g / gy, yy = g % gy;
         const int zlo = zb[zz], zhi = zb[zz + 1], ylo = yb[yy], yhi = yb[yy + 1];
         uint32_t *cs = colsum + (g & 1) * a.nx;
-        if (kVec) accumulate_row_vec<T, kMode, kPacked>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
-        else accumulate_row_scalar<T, kMode>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
+        accumulate_row_vec<T, kMode, kPacked, kVec>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
         __syncthreads();
         const uint32_t R = uint32_t((zhi - zlo) * (yhi - ylo));
         T *row = atlas_ptr(a.atlas[0], a.pitch[0], a.tiles_x[0], a.mx, a.my, 0, Y0 + yy, Z0 + zz);
@@ -185,7 +244,8 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
     const int mode = load_keep_table(a.keep, a.nbins, a.shift, a.limit, lut, sh_keep, int(threadIdx.x),
                                      int(blockDim.x), &lo, [] { __syncthreads(); });
     uint16_t *g0 = a.fused ? grp : nullptr;
-    if (mode == 0) level0_group<T, kVec, 0, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    if (mode == 0 && sizeof(T) == 1 && a.packed) level0_group<T, kVec, 0, true>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else if (mode == 0) level0_group<T, kVec, 0, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
     else if (mode == 1) level0_group<T, kVec, 1, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
     else if (a.packed) level0_group<T, kVec, 2, true>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
     else level0_group<T, kVec, 2, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
@@ -351,7 +411,7 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
         const int gz = 1 << fused, gy = 1 << fused;
         // two 16-bit lanes per word stay exact when a footprint's sum fits 16 bits
         const int64_t rmax = ((d->ny + a.my - 1) / a.my) * ((d->nz + a.mz - 1) / a.mz);
-        a.packed = sizeof(T) == 2 && d->bits <= 15 && rmax * ((int64_t(1) << d->bits) - 1) < 65536;
+        a.packed = d->bits <= 15 && rmax * ((int64_t(1) << d->bits) - 1) < 65536;
         size_t smem = size_t(2) * a.nx * 4 + size_t(a.mx + 1 + gz + 1 + gy + 1) * 4;
         if (fused) smem += size_t(gz) * gy * a.mx * 2;
         if (fused > 1) smem += size_t(gz / 2) * (gy / 2) * (a.mx / 2) * 2;

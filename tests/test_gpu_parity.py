@@ -223,6 +223,34 @@ def test_slicemap_packed_path_with_out_of_depth_values(env, T):
     _check_atlases(sm, oracle.slicemap(vol, 12, dims, keep_ref), oracle)
 
 
+@pytest.mark.parametrize("shape,bits,mode", [((29, 37, 385), 8, "otsu"), ((29, 37, 385), 8, "topslab"),
+                                             ((29, 37, 385), 8, None), ((23, 19, 101), 12, "otsu"),
+                                             ((23, 19, 101), 12, None), ((40, 33, 999), 8, "its")])
+def test_slicemap_unaligned_rows(env, shape, bits, mode):
+    # rows that do not start on 16-byte boundaries (the batched workload's
+    # volumes have random sizes), plus an unaligned base pointer (z >= 1 slab)
+    mctp, oracle, phantom, dev = env
+    nz, ny, nx = shape
+    spec = phantom.VolumeSpec(nx, ny, nz, bits=bits, seed=nx + ny, n_ell=5)
+    full = phantom.generate_cpu(spec)
+    for vol in (full, full[1:]):
+        vol = np.ascontiguousarray(vol)
+        nbins = 256 if bits == 8 else 4096
+        keep_ref = None
+        if mode == "topslab":
+            keep_ref = oracle.keep_topslab(oracle.histogram(vol, bits, nbins, 0, 3)[0], 1)
+        elif mode is not None:
+            h, _ = oracle.histogram(vol, bits, nbins)
+            keep_ref = oracle.keep_threshold(nbins, oracle.otsu(h)[0] if mode == "otsu" else oracle.its(h)[0])
+        dims = [(vol.shape[2] // 3 // 2 * 2, vol.shape[1] // 2 // 2 * 2, vol.shape[0] // 2 // 2 * 2)]
+        dims.append(tuple(d // 2 for d in dims[0]))
+        g = torch.from_numpy(full).to(dev)[1:] if vol.shape != full.shape else up(vol, dev)
+        sm = mctp.Slicemap.allocate((vol.shape[2], vol.shape[1], vol.shape[0]), dims[0], 2,
+                                    torch.from_numpy(vol[:1, :1, :1]).dtype, bits, dev)
+        mctp.build_slicemap(g, bits, sm, up(keep_ref, dev) if keep_ref is not None else None)
+        _check_atlases(sm, oracle.slicemap(vol, bits, dims, keep_ref), oracle)
+
+
 def test_slicemap_custom_tiles(env):
     mctp, oracle, phantom, dev = env
     vol = phantom.generate_cpu(phantom.VolumeSpec(64, 48, 52, bits=8, seed=12, n_ell=4))
