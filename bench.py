@@ -9,7 +9,13 @@ steps.  The input (14.6 GB) is larger than L2, so no flush is needed between
 steps.  Multi-GPU runs are independent replicas (weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mctp|reference]
-                  [--workload full|small]
+                  [--workload full|mid|slab|small|batch]
+
+--workload batch: 64 u8 phantoms with axes ~ U{384..1024} (22 GB resident),
+each through histogram, Otsu and a 256^3 slicemap, then 12 views of each at
+512 x 512 in one persistent render launch, the whole pass replayed as one
+CUDA graph; the line also times the plain per-volume and per-view render
+launches on the same slicemaps.
 """
 from __future__ import annotations
 
@@ -50,6 +56,13 @@ def workload(name: str):
                     az_step=10.0, desc="slab (profiling): u16 12-bit 2016x2016x224 phantom (1.8 GB) with the full "
                                        "workload's footprints, 4096 bins, Otsu, levels 512x512x64/256x256x32/"
                                        "128x128x16, 4 views 1024x1024")
+    if name == "batch":
+        specs = phantom.batch_specs(64)
+        return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=1, nviews=12,
+                    size=512, az_step=30.0, elevation=20.0,
+                    desc="batch: 64 u8 phantoms, axes ~U{384..1024} (%.1f GB), 256 bins, Otsu, one 256^3 level "
+                         "each, 12 views 512x512 (az 30k deg, el 20 deg), step 0.5, ramp LUT, one persistent "
+                         "render launch, CUDA graph" % (sum(sp.nbytes for sp in specs) / 1e9))
     spec = phantom.SMALL
     return dict(spec=spec, bits=8, nbins=256, level0=(128, 128, 128), nlevels=1, nviews=1, size=256,
                 az_step=0.0, desc="small: u8 256^3 phantom, 256 bins, Otsu, level 128^3, 1 view 256x256")
@@ -397,18 +410,231 @@ def run_gpu(args, wl):
     return 0
 
 
+def run_batch(args, wl):
+    """The batched workload (replicas only for N > 1, like the single-volume path)."""
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    from paper_2311_15038_gb300 import batch as bt
+    from paper_2311_15038_gb300 import pipeline as pl
+    mctp._lib.load()
+
+    specs = wl["specs"]
+    vols = []
+    for sp in specs:
+        v = torch.empty(sp.shape, dtype=torch.uint8, device=dev)
+        phantom.generate_gpu(sp, v)
+        vols.append(v)
+    lut = torch.from_numpy(phantom.ramp_lut(256)).to(dev)
+    views = pl.turntable(wl["nviews"], wl["size"], 0, 0.5, wl["elevation"], wl["az_step"])
+    stream = torch.cuda.Stream(dev)
+    items = [bt.BatchItem(v, 8, views, 0) for v in vols]
+    pipe = bt.BatchPipeline(items, wl["level0"], wl["nlevels"], lut, wl["nbins"], "otsu", 0.99, device=dev,
+                            stream=stream)
+    best, tune_ms = pipe.autotune(reps=2)
+    torch.cuda.synchronize(dev)
+
+    # ---- the plain per-volume and per-view launches on the same slicemaps; the
+    # batched images must equal them bit for bit
+    n_views = len(pipe.views)
+    total = pipe.images.numel()
+    plain = torch.empty_like(pipe.images)
+    plain_samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    per_vol_samples = [torch.empty(1, dtype=torch.uint64, device=dev) for _ in items]
+    per_view_samples = [torch.empty(1, dtype=torch.uint64, device=dev) for _ in range(n_views)]
+    px = wl["size"] * wl["size"] * 4
+
+    def per_volume():
+        for i, sm in enumerate(pipe.slicemaps):
+            o = plain[i * len(views) * px:(i + 1) * len(views) * px]
+            mctp.render_views(sm, views, lut, 0.99, o, per_vol_samples[i], stream)
+
+    def per_view():
+        for j in range(n_views):
+            sm = pipe.slicemaps[pipe.view_slicemap[j]]
+            mctp.render_views(sm, [pipe.views[j]], lut, 0.99, plain[j * px:(j + 1) * px], per_view_samples[j],
+                              stream)
+
+    def batched():
+        pipe.render()
+
+    def timed(fn, reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            fn()
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    t_batched = timed(batched, 3)
+    samples_per_step = int(pipe.samples.item())
+    ref_images = pipe.images.clone()
+    t_per_volume = timed(per_volume, 3)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(plain[:total], ref_images[:total]), "batched images differ from per-volume launches"
+    assert sum(int(s.item()) for s in per_vol_samples) == samples_per_step
+    t_per_view = timed(per_view, 3)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(plain[:total], ref_images[:total]), "batched images differ from per-view launches"
+    assert sum(int(s.item()) for s in per_view_samples) == samples_per_step
+
+    # ---- stage split from one eager pass, then the graph
+    ev = {}
+
+    def timer(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        ev.setdefault(name, []).append(e)
+
+    with torch.cuda.stream(stream):
+        pipe.run(timer)
+    torch.cuda.synchronize(dev)
+    stage_ms = dict(prepare=ev["prepare"][0].elapsed_time(ev["render"][0]),
+                    render=ev["render"][0].elapsed_time(ev["end"][0]))
+    pipe.capture()
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            pipe.replay()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    step_events = []
+    t0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pipe.replay()
+            b.record(stream)
+            step_events.append((a, b))
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    assert int(pipe.samples.item()) == samples_per_step
+    assert torch.equal(pipe.images, ref_images)
+    if ws > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    step_ms = [a.elapsed_time(b) for a, b in step_events]
+
+    # ---- end to end: every volume from pinned host memory, every image back
+    vol_bytes = sum(sp.nbytes for sp in specs)
+    hosts = []
+    for v in vols:
+        h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+        h.copy_(v)
+        hosts.append(h)
+    img_host = torch.empty(pipe.images.shape, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            for v, h in zip(vols, hosts):
+                v.copy_(h, non_blocking=True)
+            pipe.replay()
+            img_host.copy_(pipe.images, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
+    del hosts
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    atlas_bytes = sum(sm.nbytes for sm in pipe.slicemaps)
+    prep_bytes = 2 * vol_bytes + atlas_bytes   # histogram read + slicemap read + atlas writes
+    render_s = stage_ms["render"] / 1e3
+    ach = FP32_FLOPS_PER_SAMPLE * samples_per_step / render_s / 1e12
+    roof = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak, kernel="render",
+                ms=stage_ms["render"], traffic=None, peak_source="FP32 issue rate at the maximum SM clock")
+    value = samples_per_step * args.steps * ws / elapsed
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+        ms_per_step=elapsed * 1e3 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="u8/f32", data="synthetic",
+        config=dict(workload=wl["desc"], l2="inputs larger than L2 (%.1f GB of volumes; no flush)" % (vol_bytes / 1e9),
+                    parallelism=f"replicas x{ws}", tuning=dict(warp_w=best.warp_w, chunk=best.chunk,
+                                                               ctas_per_sm=best.ctas_per_sm)),
+        samples_per_step=samples_per_step,
+        stage_ms=stage_ms,
+        prepare_gbs=prep_bytes / (stage_ms["prepare"] / 1e3) / 1e9,
+        prepare_frac_of_hbm_peak=prep_bytes / (stage_ms["prepare"] / 1e3) / 1e9 / pk["hbm_gbs"],
+        render_samples_per_s=dict(batched=samples_per_step / t_batched, per_volume=samples_per_step / t_per_volume,
+                                  per_view=samples_per_step / t_per_view),
+        render_ms=dict(batched=t_batched * 1e3, per_volume=t_per_volume * 1e3, per_view=t_per_view * 1e3),
+        batched_equals_plain=True,
+        autotune_ms={f"w{t.warp_w}c{t.chunk}k{t.ctas_per_sm}": ms for t, ms in tune_ms.items()},
+        latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
+        roofline=roof,
+        gpu_launches=(4 * len(items) + 1 + (n_views + 127) // 128 + 1) * args.steps,
+        clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
+        e2e=dict(value=samples_per_step / e2e_s, unit=UNIT, h2d_bytes_per_step=vol_bytes,
+                 d2h_bytes_per_step=pipe.images.numel() * 4, ms_per_step=e2e_s * 1e3),
+    )
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sp = specs[0]
+        wl0 = dict(wl, spec=sp)
+        nz_s = min(sp.nz, 96)
+        zs = sp.nz // 2 - nz_s // 2
+        step_s, samples_step, text = oracle_sample(wl0, vols[0][zs:zs + nz_s].cpu().numpy(), npix=65536)
+        line["cpu_baseline"] = dict(value=samples_step / step_s, unit=UNIT, cores=1, kind="oracle",
+                                    sample="volume 0 of the batch: " + text)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small"])
+    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.workload == "batch":
+        return run_batch(args, wl)
     return run_gpu(args, wl)
 
 

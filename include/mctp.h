@@ -221,6 +221,54 @@ int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views, int32_t n
                       const float *lut_rgba, int32_t nlut, float alpha_stop, float *out_rgba,
                       uint64_t *samples_taken, void *stream);
 
+/*
+ * Batched rendering: the views of many slicemaps in one persistent launch
+ * (the paper renders one view per request, Sec. III-C; batching many volumes
+ * and views is an extension of this library).  View i is rendered from
+ * level views[i].level of sms[view_slicemap[i]] with transfer function
+ * view_lut[i], exactly as mctp_render_views would render it alone: images
+ * and sample counts are bit-identical.  Work is a queue of 32-ray warp tiles
+ * over all views, taken by persistent warps with an atomic counter.
+ *   sms           host array of nsm slicemaps, all of one dtype
+ *   views, view_slicemap, view_lut  host arrays of nviews entries
+ *   luts_rgba     device float[nluts][nlut][4] (layout of mctp_render_views'
+ *                 lut_rgba, one table after another), 2 <= nlut <= 4096
+ *   tuning        NULL or a mctp_batch_tuning (below); it changes speed only
+ *   out_rgba      device float, 16-byte aligned; view i is an
+ *                 [height][width][4] image after the images of views 0..i-1
+ *   samples_taken device uint64[1] or NULL: overwritten with the samples
+ *                 marched over all rays of the batch
+ *   workspace     device memory of at least the size that
+ *                 mctp_render_batch_workspace gives for the same arguments,
+ *                 256-byte aligned, owned by the caller; its contents need no
+ *                 initialisation and are rewritten by every call, so two
+ *                 calls in flight at once must not share it
+ * Everything is enqueued on `stream` (kernel launches and memsets only; no
+ * host synchronisation), so a call can be captured in a CUDA graph.
+ * Errors: MCTP_EINVAL (null pointers, an index out of range, bad view,
+ *         nlut or alpha_stop out of range, bad tuning, misaligned pointer),
+ *         MCTP_EUNSUPPORTED (slicemaps of different dtypes), MCTP_ESIZE
+ *         (workspace too small, a view larger than 2^28 pixels, more than
+ *         2^31 warp tiles in the batch), MCTP_ECUDA.
+ */
+typedef struct {
+    int32_t warp_w;      /* pixels per warp row: 4, 8, 16 or 32 (a warp covers
+                            warp_w x 32/warp_w pixels); 0 = 8 */
+    int32_t chunk;       /* warp tiles taken per queue access, 1..64; 0 = 2 */
+    int32_t ctas_per_sm; /* cap on resident CTAs per SM; 0 = occupancy limit */
+    int32_t reserved;    /* must be 0 */
+} mctp_batch_tuning;
+
+int mctp_render_batch_workspace(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
+                                const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,
+                                int32_t nluts, size_t *bytes);
+
+int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
+                      const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,
+                      const float *luts_rgba, int32_t nluts, int32_t nlut, float alpha_stop,
+                      const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
 /* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
  * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
 int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);

@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import MctpError  # noqa: F401
 
 __all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
-           "Slicemap", "View", "default_tiles", "atlas_bytes", "version", "MctpError"]
+           "render_batch", "render_batch_workspace", "BatchTuning", "Slicemap", "View", "default_tiles",
+           "atlas_bytes", "version", "MctpError"]
 
 _DTYPES = {torch.uint8: (_lib.MCTP_U8, 1), torch.uint16: (_lib.MCTP_U16, 2), torch.int16: (_lib.MCTP_U16, 2)}
 _MODES = {"otsu": _lib.MCTP_THR_OTSU, "its": _lib.MCTP_THR_ITS, "topslab": _lib.MCTP_THR_TOPSLAB,
@@ -222,3 +223,78 @@ def images(flat: torch.Tensor, views) -> list[torch.Tensor]:
         out.append(flat[off:off + n].view(v.height, v.width, 4))
         off += n
     return out
+
+
+@dataclass(frozen=True)
+class BatchTuning:
+    """Launch shape of render_batch (speed only; results do not depend on it)."""
+    warp_w: int = 8       # a warp covers warp_w x 32/warp_w pixels (4, 8, 16 or 32)
+    chunk: int = 2        # warp tiles taken per queue access (1..64)
+    ctas_per_sm: int = 0  # cap on resident CTAs per SM (0 = occupancy limit)
+
+    def c(self) -> _lib.BatchTuning:
+        return _lib.BatchTuning(self.warp_w, self.chunk, self.ctas_per_sm, 0)
+
+
+class _BatchArgs:
+    """Host arrays of one batch (slicemap descriptors, views, indices)."""
+
+    def __init__(self, slicemaps, views, view_slicemap, view_lut):
+        n = len(views)
+        if len(view_slicemap) != n or len(view_lut) != n:
+            raise ValueError("views, view_slicemap and view_lut differ in length")
+        self.sms = (_lib.SlicemapDesc * max(1, len(slicemaps)))()
+        for i, sm in enumerate(slicemaps):
+            self.sms[i] = sm.desc()
+        self.nsm = len(slicemaps)
+        self.views = view_array(views)
+        self.vsm = (_lib.C_I32 * max(1, n))(*view_slicemap)
+        self.vlut = (_lib.C_I32 * max(1, n))(*view_lut)
+        self.n = n
+
+
+def _luts3(luts: torch.Tensor) -> torch.Tensor:
+    _cuda(luts, "luts")
+    if luts.dim() == 2:
+        luts = luts.unsqueeze(0)
+    if luts.dtype != torch.float32 or luts.dim() != 3 or luts.shape[2] != 4:
+        raise ValueError("luts must be float32 [nluts][nlut][4] (or [nlut][4])")
+    return luts
+
+
+def render_batch_workspace(slicemaps, views, view_slicemap, view_lut, nluts: int) -> int:
+    """Bytes of device workspace render_batch needs for this batch."""
+    a = _BatchArgs(slicemaps, views, view_slicemap, view_lut)
+    nb = ctypes.c_size_t()
+    _lib.check(_lib.load().mctp_render_batch_workspace(a.sms, a.nsm, a.views, a.vsm, a.vlut, a.n, nluts,
+                                                       ctypes.byref(nb)), "mctp_render_batch_workspace")
+    return nb.value
+
+
+def render_batch(slicemaps, views, view_slicemap, view_lut, luts: torch.Tensor, alpha_stop: float = 0.99,
+                 tuning: BatchTuning | None = None, out: torch.Tensor | None = None,
+                 samples: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
+    """Render view i from slicemaps[view_slicemap[i]] with luts[view_lut[i]], all in one persistent launch.
+
+    Returns (flat float32 RGBA buffer, samples uint64[1], workspace); images() splits the buffer.
+    Pass the returned workspace back in to reuse it (e.g. for CUDA-graph capture)."""
+    luts = _luts3(luts)
+    a = _BatchArgs(slicemaps, views, view_slicemap, view_lut)
+    dev = luts.device
+    nb = ctypes.c_size_t()
+    lib = _lib.load()
+    _lib.check(lib.mctp_render_batch_workspace(a.sms, a.nsm, a.views, a.vsm, a.vlut, a.n, luts.shape[0],
+                                               ctypes.byref(nb)), "mctp_render_batch_workspace")
+    if workspace is None:
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    _cuda(workspace, "workspace")
+    total = sum(v.width * v.height * 4 for v in views)
+    if out is None:
+        out = torch.empty(max(total, 4), dtype=torch.float32, device=dev)
+    if samples is None:
+        samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    t = (tuning or BatchTuning()).c()
+    _lib.check(lib.mctp_render_batch(a.sms, a.nsm, a.views, a.vsm, a.vlut, a.n, _ptr(luts), luts.shape[0],
+                                     luts.shape[1], alpha_stop, ctypes.byref(t), _ptr(out), _ptr(samples),
+                                     _ptr(workspace), workspace.numel(), _stream(stream)), "mctp_render_batch")
+    return out, samples, workspace

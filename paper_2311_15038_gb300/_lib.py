@@ -49,6 +49,10 @@ class ViewDesc(ctypes.Structure):
                 ("width", C_I32), ("height", C_I32), ("level", C_I32), ("step", ctypes.c_float)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("warp_w", C_I32), ("chunk", C_I32), ("ctas_per_sm", C_I32), ("reserved", C_I32)]
+
+
 EXPORTS = {
     "mctp_build_histogram": ([C_VP, ctypes.POINTER(VolumeDesc), C_I64, C_I64, C_I32, C_VP, C_VP, C_VP],
                              ctypes.c_int),
@@ -58,6 +62,11 @@ EXPORTS = {
                             ctypes.c_int),
     "mctp_render_views": ([ctypes.POINTER(SlicemapDesc), ctypes.POINTER(ViewDesc), C_I32, C_VP, C_I32,
                            ctypes.c_float, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_render_batch_workspace": ([ctypes.POINTER(SlicemapDesc), C_I32, ctypes.POINTER(ViewDesc), C_VP, C_VP,
+                                     C_I32, C_I32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "mctp_render_batch": ([ctypes.POINTER(SlicemapDesc), C_I32, ctypes.POINTER(ViewDesc), C_VP, C_VP, C_I32,
+                           C_VP, C_I32, C_I32, ctypes.c_float, ctypes.POINTER(BatchTuning), C_VP, C_VP, C_VP,
+                           ctypes.c_size_t, C_VP], ctypes.c_int),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),

@@ -1,42 +1,17 @@
-// render.cu -- server-side rendering of slicemap views (Sec. III-C):
-// orthographic emission-absorption ray marching, front to back, with
+// render.cu -- server-side rendering of slicemap views (Sec. III-C) in one
+// call: orthographic emission-absorption ray marching, front to back, with
 // trilinear sampling of a slicemap level, a 1D RGBA transfer function and
-// early ray termination.
-//
-// Per ray:
-//  * set-up in FP32 with one rounding per operation in a fixed order (camera
-//    origin, slab intersection, sample count n = floor((t_far - t_near) /
-//    Delta)), so n matches any other IEEE implementation of the same steps;
-//  * the level coordinate of sample k is q0 + k dq, held as 32.32 fixed-point
-//    integers: dq once per view on the host (FP64), q0 once per ray in
-//    float-float arithmetic (no FP64, which runs at a small fraction of the
-//    FP32 rate on this part), so stepping is exact integer arithmetic and a
-//    sample position is accurate to ~1e-9 voxel (an FP32 position would carry
-//    ~3e-5 voxel of rounding at 512 voxels);
-//  * trilinear interpolation of the atlas in FP32 (corner indices clamped to
-//    the level), transfer-function lookup with linear interpolation from
-//    shared memory, premultiplied over-compositing, exit once A >= alpha_stop.
+// early ray termination.  The per-ray march lives in render_common.cuh.
 //
 // Empty-space skipping: when the level has a max grid, every CTA turns it
-// into a shared-memory bitmap of the 8^3 cells whose maximum (over the cell
-// plus one voxel, i.e. every voxel a sample with its lower corner in the cell
-// reads) can produce a nonzero opacity under this call's transfer function.
-// A sample whose lower corner lies in an unmarked cell has opacity exactly 0
-// (all its corners are at or below a value whose lookup lands on zero-opacity
-// entries, evaluated with the same FP32 operations as a full sample), so it
-// adds exactly nothing to C and A and is not evaluated: an exact integer DDA
-// over the cells gives the index of the first sample of the next cell, and the
-// march jumps there at once.  Images and sample counts equal those of a full
-// march.
+// into a shared-memory bitmap of the cells that can produce a nonzero opacity
+// under this call's transfer function (see render_common.cuh for why skipping
+// them is exact).
 //
 // CTAs are persistent (one wave sized by occupancy) and walk the 16 x 16 pixel
 // tiles of all views in order; a warp covers an 8 x 4 pixel sub-tile so its
 // rays sample neighbouring texels together.
-#include <math.h>
-
-#include <algorithm>
-
-#include "mctp_internal.cuh"
+#include "render_common.cuh"
 
 namespace mctp {
 
@@ -44,27 +19,11 @@ int check_slicemap(const mctp_slicemap *sm);
 
 namespace {
 
-constexpr int kMaxViewsPerLaunch = 64;
-constexpr int kTileW = 16, kTileH = 16;
-constexpr int kRenderThreads = kTileW * kTileH;
-constexpr int kMaxLut = 4096;
-constexpr int kMaxBitmapWords = 8192;  // 64^3 cells
+using namespace render;
 
-struct ViewParams {
-    float b[3], r[3], u[3];
-    float c[3], N[3];
-    float L, delta;
-    int32_t W, H;
-    int32_t tiles_w;  // image tiles along x
-    int32_t level;
-    float sc_hi[3], sc_lo[3];  // M_a / N_a as an unevaluated float sum
-    float inv_m[3];            // 1 / |dU| (0 when dU == 0)
-    long long dU[3];           // fixed-point step of the level coordinate per sample
-    uint32_t qq[3], rr[3];     // 8 voxels (fixed point) = qq |dU| + rr (qq capped at 2^30)
-    int32_t skip_ok;           // |dU| < 2^32 on every axis: the cell DDA runs in 32 bits
-    int64_t out_offset;  // in floats
-    int64_t tile_begin;  // first tile of this view
-};
+constexpr int kMaxViewsPerLaunch = 64;
+constexpr int kRenderThreads = kTileW * kTileH;
+constexpr int kMaxBitmapWords = 8192;  // 64^3 cells
 
 struct LevelParams {
     const void *atlas;
@@ -92,72 +51,6 @@ struct RenderParams {
 };
 
 template <typename T>
-__device__ __forceinline__ float texel(const T *atlas, uint32_t off)
-{
-    return float(__ldg(atlas + off));
-}
-
-// Error-free transformations (Knuth's TwoSum; the FMA TwoProduct): a + b and
-// a * b as an unevaluated sum hi + lo of two floats.
-__device__ __forceinline__ void two_sum(float a, float b, float &hi, float &lo)
-{
-    hi = __fadd_rn(a, b);
-    const float bb = __fsub_rn(hi, a);
-    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void two_prod(float a, float b, float &hi, float &lo)
-{
-    hi = __fmul_rn(a, b);
-    lo = fmaf(a, b, -hi);
-}
-
-// Fixed-point (32.32) level coordinate (o + t0 d) * sc - 1/2 of a ray's first
-// sample, t0 = tn + h, in float-float arithmetic (relative error ~2^-44): no
-// FP64 on the per-ray path.
-__device__ __forceinline__ long long start_coord(float o, float d, float tn, float h, float sc_hi, float sc_lo)
-{
-    float t_hi, t_lo, p_hi, p_lo, s_hi, s_lo, m_hi, m_lo;
-    two_sum(tn, h, t_hi, t_lo);
-    two_prod(t_hi, d, p_hi, p_lo);
-    p_lo = fmaf(t_lo, d, p_lo);
-    two_sum(o, p_hi, s_hi, s_lo);
-    s_lo = __fadd_rn(s_lo, p_lo);
-    two_prod(s_hi, sc_hi, m_hi, m_lo);
-    m_lo = fmaf(s_hi, sc_lo, fmaf(s_lo, sc_hi, m_lo));
-    return __float2ll_rn(__fmul_rn(m_hi, 4294967296.0f)) + __float2ll_rn(__fmul_rn(m_lo, 4294967296.0f)) -
-           (1LL << 31);
-}
-
-// Lookup coordinate of a raw interpolated value, as the march computes it.
-__device__ __forceinline__ float lut_coord(float raw, float inv_vmax, float nl1)
-{
-    return __fmul_rn(fminf(__fmul_rn(raw, inv_vmax), 1.0f), nl1);
-}
-
-// Largest raw grey value S such that every sample whose corners are all <= S
-// has opacity exactly 0 under the transfer function in shared memory; -1 when
-// none.  Corners <= S give an interpolated value below S + 1, whose lookup
-// coordinate is <= that of S + 1; if that coordinate is <= zmax (entries
-// 0..zmax have zero opacity) the interpolated opacity is exactly 0.  All-zero
-// corners interpolate to exactly 0, which is enough when entry 0 is zero.
-__device__ int skip_threshold(const float4 *lut, int nlut, float inv_vmax, int vmax_int)
-{
-    int zmax = -1;
-    while (zmax + 1 < nlut && lut[zmax + 1].w == 0.0f) ++zmax;
-    if (zmax < 0) return -1;
-    const float nl1 = float(nlut - 1), zf = float(zmax);
-    int lo = -1, hi = vmax_int;  // invariant: lo satisfies (or is -1), hi + 1 fails or hi is the top
-    if (lut_coord(float(vmax_int) + 1.0f, inv_vmax, nl1) <= zf) return vmax_int;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) / 2;
-        if (lut_coord(float(mid) + 1.0f, inv_vmax, nl1) <= zf) lo = mid;
-        else hi = mid;
-    }
-    return max(lo, 0);  // zmax >= 0 means entry 0 is zero, so all-zero cells always skip
-}
-
-template <typename T>
 __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_constant__ RenderParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -176,7 +69,8 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
     unsigned long long taken_total = 0;
     int v = 0, cur_level = -1;
     bool use_skip = false;
-    int gy = 0, wpr = 1;
+    LevelGeom G{};
+    const SharedTables tab{lut, slice_off, occ};
 
     for (int64_t tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
         while (v + 1 < P.nviews && tile >= P.view[v + 1].tile_begin) ++v;
@@ -190,22 +84,17 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
                 slice_off[z] = uint32_t(int64_t(row) * Lv.my * Lv.pitch + int64_t(col) * Lv.mx);
             }
             // occupancy bitmap, one bit per cell, rows of wpr words per (cz, cy)
-            wpr = (Lv.gx + 31) / 32;
+            G.m1[0] = Lv.mx - 1;
+            G.m1[1] = Lv.my - 1;
+            G.m1[2] = Lv.mz - 1;
+            G.pitch = uint32_t(Lv.pitch);
+            G.wpr = (Lv.gx + 31) / 32;
+            G.gy = Lv.gy;
             const int nrows = Lv.gy * Lv.gz;
-            gy = Lv.gy;
-            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && int64_t(nrows) * wpr <= kMaxBitmapWords;
-            if (use_skip) {
-                // exact bits: a cell is marked when its maximum exceeds S
-                for (int w = threadIdx.x; w < nrows * wpr; w += blockDim.x) {
-                    const int r = w / wpr, wx = w - r * wpr;
-                    uint32_t bits = 0;
-                    for (int b = 0; b < 32; ++b) {
-                        const int cx = wx * 32 + b;
-                        if (cx < Lv.gx && int(__ldg(Lv.maxgrid + int64_t(r) * Lv.gx + cx)) > skip_S) bits |= 1u << b;
-                    }
-                    occ[w] = bits;
-                }
-            }
+            use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && int64_t(nrows) * G.wpr <= kMaxBitmapWords;
+            if (use_skip)
+                for (int w = threadIdx.x; w < nrows * G.wpr; w += blockDim.x)
+                    occ[w] = occupancy_word(Lv.maxgrid, Lv.gx, G.wpr, w, skip_S);
             __syncthreads();
         }
 
@@ -213,148 +102,8 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
         const int px = int(t % V.tiles_w) * kTileW + (warp & 1) * 8 + (lane & 7);
         const int py = int(t / V.tiles_w) * kTileH + (warp >> 1) * 4 + (lane >> 3);
         if (px >= V.W || py >= V.H) continue;
-
-        // ---- FP32 ray set-up, one rounding per operation, fixed order
-        const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
-        const float sy = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn(float(py), 0.5f), float(V.H)));
-        const float sxL = __fmul_rn(sx, V.L), syL = __fmul_rn(sy, V.L);
-        float o[3], d[3];
-        float tmin = -INFINITY, tmax = INFINITY;
-        bool miss = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float t1 = __fadd_rn(V.c[a], __fmul_rn(sxL, V.r[a]));
-            const float t2 = __fadd_rn(t1, __fmul_rn(syL, V.u[a]));
-            o[a] = __fadd_rn(t2, __fmul_rn(V.L, V.b[a]));
-            d[a] = -V.b[a];
-            if (d[a] != 0.0f) {
-                const float inv = __frcp_rn(d[a]);
-                const float s0 = __fmul_rn(__fsub_rn(0.0f, o[a]), inv);
-                const float s1 = __fmul_rn(__fsub_rn(V.N[a], o[a]), inv);
-                tmin = fmaxf(tmin, fminf(s0, s1));
-                tmax = fminf(tmax, fmaxf(s0, s1));
-            } else if (!(o[a] >= 0.0f && o[a] <= V.N[a])) {
-                miss = true;
-            }
-        }
-        int64_t n = 0;
-        if (!miss && tmax > tmin) n = int64_t(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
-
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n > 0) {
-            // ---- fixed-point level coordinates of sample 0; the step is per view
-            long long U0[3];
-            const long long *dU = V.dU;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                U0[a] = start_coord(o[a], d[a], tmin, 0.5f * V.delta, V.sc_hi[a], V.sc_lo[a]);
-            const int Mm1[3] = {Lv.mx - 1, Lv.my - 1, Lv.mz - 1};
-            // ---- exact integer DDA over the 8^3 cells of each sample's lower
-            // corner: nxt[a] is the first sample index whose corner is in the
-            // next cell along axis a; with m = |dU| (< 2^32), D = 8 voxels,
-            // D = q m + r, the crossing after one at c (slack e = c m -
-            // distance, 0 <= e < m) is at c + q + (r > e), slack
-            // e + (r > e ? m : 0) - r.  Indices past the ray's end stand for
-            // "no further crossing".
-            const bool skip = use_skip && V.skip_ok;
-            constexpr int kInf = 0x7fffffff;
-            int cc[3], nxt[3];
-            uint32_t ee[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                cc[a] = min(max(int(U0[a] >> 32), 0), Mm1[a]) >> 3;
-                nxt[a] = kInf;
-                ee[a] = 0;
-                const int last = Mm1[a] >> 3;
-                if (skip && dU[a] != 0 && (dU[a] > 0 ? cc[a] < last : cc[a] > 0)) {
-                    const long long m = dU[a] > 0 ? dU[a] : -dU[a];
-                    const long long num = dU[a] > 0 ? ((long long)(8 * cc[a] + 8) << 32) - U0[a]
-                                                    : U0[a] - ((long long)(8 * cc[a]) << 32) + 1;
-                    // c = ceil(num / m): float estimate, then exact correction
-                    const float est = float(num) * V.inv_m[a];
-                    if (est < float(n) + 2.0f) {
-                        long long c = (long long)est;
-                        while (c * m < num) ++c;
-                        while (c > 0 && (c - 1) * m >= num) --c;
-                        nxt[a] = int(c);
-                        ee[a] = uint32_t(c * m - num);
-                    }
-                }
-            }
-            auto cross = [&](int a) {
-                const bool fwd = dU[a] > 0;
-                cc[a] += fwd ? 1 : -1;
-                if (fwd ? cc[a] >= (Mm1[a] >> 3) : cc[a] <= 0) {
-                    nxt[a] = kInf;  // the last cell this way: clamping keeps the corner in it
-                    return;
-                }
-                const uint32_t m = uint32_t(fwd ? dU[a] : -dU[a]);
-                const bool up = V.rr[a] > ee[a];
-                nxt[a] = int(min(uint32_t(nxt[a]) + V.qq[a] + (up ? 1u : 0u), uint32_t(kInf)));
-                ee[a] += (up ? m : 0u) - V.rr[a];
-            };
-            const T *atlas = static_cast<const T *>(Lv.atlas);
-            const uint32_t pitch = uint32_t(Lv.pitch);
-            const float nl1 = float(P.nlut - 1);
-            const int jmax = P.nlut - 2;
-            float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-            int k = 0;
-            const int nn = int(n);
-            while (k < nn) {
-                if (skip) {
-                    const uint32_t word = occ[(cc[2] * gy + cc[1]) * wpr + (cc[0] >> 5)];
-                    if (!((word >> (cc[0] & 31)) & 1u)) {
-                        // an empty cell: its samples have opacity exactly 0; jump
-                        // to the first sample of the next cell
-                        const int kn = min(min(nxt[0], nxt[1]), nxt[2]);
-                        if (kn >= nn) { k = nn; break; }
-                        k = kn;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            if (nxt[a] == kn) cross(a);
-                        continue;
-                    }
-                }
-                long long U[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) U[a] = U0[a] + (long long)k * dU[a];
-                const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
-                const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]), z0i = min(max(iz, 0), Mm1[2]);
-                const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
-                const int z1i = min(max(iz + 1, 0), Mm1[2]);
-                const float fx = float(uint32_t(U[0])) * 2.3283064365386963e-10f;
-                const float fy = float(uint32_t(U[1])) * 2.3283064365386963e-10f;
-                const float fz = float(uint32_t(U[2])) * 2.3283064365386963e-10f;
-                const uint32_t za = slice_off[z0i], zb = slice_off[z1i];
-                const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
-                const float v000 = texel(atlas, za + ya + x0), v100 = texel(atlas, za + ya + x1);
-                const float v010 = texel(atlas, za + yb + x0), v110 = texel(atlas, za + yb + x1);
-                const float v001 = texel(atlas, zb + ya + x0), v101 = texel(atlas, zb + ya + x1);
-                const float v011 = texel(atlas, zb + yb + x0), v111 = texel(atlas, zb + yb + x1);
-                const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
-                const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
-                const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-                const float x = lut_coord(fmaf(fz, c1 - c0, c0), P.inv_vmax, nl1);
-                const int j = min(int(x), jmax);
-                const float fl = x - float(j);
-                const float4 e0 = lut[j], e1 = lut[j + 1];
-                const float ca = fmaf(fl, e1.w - e0.w, e0.w);
-                const float w = (1.0f - A) * ca;
-                C0 = fmaf(w, fmaf(fl, e1.x - e0.x, e0.x), C0);
-                C1 = fmaf(w, fmaf(fl, e1.y - e0.y, e0.y), C1);
-                C2 = fmaf(w, fmaf(fl, e1.z - e0.z, e0.z), C2);
-                A += w;
-                ++k;
-                if (A >= P.alpha_stop) break;
-                if (skip) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        if (nxt[a] == k) cross(a);
-                }
-            }
-            acc = make_float4(C0, C1, C2, A);
-            taken_total += (unsigned long long)k;
-        }
+        const float4 acc = march_ray<T>(V, static_cast<const T *>(Lv.atlas), G, use_skip, tab, P.nlut,
+                                        P.inv_vmax, P.alpha_stop, px, py, taken_total);
         reinterpret_cast<float4 *>(P.out + V.out_offset)[int64_t(py) * V.W + px] = acc;
     }
     if (P.samples) {
@@ -373,6 +122,7 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
                                  uint64_t *samples_taken, void *stream)
 {
     using namespace mctp;
+    using namespace mctp::render;
     int rc = check_slicemap(sm);
     if (rc != MCTP_OK) return rc;
     if (!views || nviews < 0 || !lut_rgba || !out_rgba) return MCTP_EINVAL;
@@ -381,10 +131,8 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
     if ((reinterpret_cast<uintptr_t>(lut_rgba) & 15) || (reinterpret_cast<uintptr_t>(out_rgba) & 15))
         return MCTP_EINVAL;
     for (int i = 0; i < nviews; ++i) {
-        const mctp_view &w = views[i];
-        if (w.width < 1 || w.height < 1 || w.level < 0 || w.level >= sm->nlevels) return MCTP_EINVAL;
-        if (!(w.step >= 1.0f / 256.0f && w.step <= 64.0f)) return MCTP_EINVAL;
-        if (int64_t(w.width) * w.height > (int64_t(1) << 28)) return MCTP_ESIZE;
+        rc = check_view(views[i], sm->nlevels);
+        if (rc != MCTP_OK) return rc;
     }
     cudaStream_t s = as_stream(stream);
     if (samples_taken && cudaMemsetAsync(samples_taken, 0, sizeof(uint64_t), s) != cudaSuccess) return MCTP_ECUDA;
@@ -411,16 +159,10 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
         L.gy = (L.my + c - 1) / c;
         L.gz = (L.mz + c - 1) / c;
         L.pitch = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
-        if (int64_t(sm->tiles_x[k]) * sm->dims[k][0] * int64_t(sm->tiles_y[k]) * sm->dims[k][1] >
-            (int64_t(1) << 32))
-            return MCTP_ESIZE;  // texel offsets are 32-bit
+        if (!level_fits_32bit(sm, k)) return MCTP_ESIZE;  // texel offsets are 32-bit
         max_mz = std::max(max_mz, sm->dims[k][2]);
     }
     if (max_mz > 16384) return MCTP_ESIZE;
-    const double PI = 3.14159265358979323846;
-    const int64_t n3[3] = {sm->src_dims[0], sm->src_dims[1], sm->src_dims[2]};
-    const float L = float(sqrt(double(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2])));
-    const float N[3] = {float(n3[0]), float(n3[1]), float(n3[2])};
     const size_t smem = size_t(nlut) * sizeof(float4) + size_t(max_mz) * sizeof(uint32_t);
     auto kern = sm->dtype == MCTP_U8 ? render_kernel<uint8_t> : render_kernel<uint16_t>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -437,46 +179,7 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
         for (int i = 0; i < cnt; ++i) {
             const mctp_view &w = views[first + i];
             ViewParams &V = P.view[i];
-            const double az = (double(w.azimuth_deg) * PI) / 180.0;
-            const double el = (double(w.elevation_deg) * PI) / 180.0;
-            V.b[0] = float(cos(el) * cos(az));
-            V.b[1] = float(cos(el) * sin(az));
-            V.b[2] = float(sin(el));
-            V.r[0] = float(-sin(az));
-            V.r[1] = float(cos(az));
-            V.r[2] = 0.0f;
-            V.u[0] = float(-sin(el) * cos(az));
-            V.u[1] = float(-sin(el) * sin(az));
-            V.u[2] = float(cos(el));
-            const int *M = sm->dims[w.level];
-            float sa[3];
-            for (int a = 0; a < 3; ++a) {
-                V.N[a] = N[a];
-                V.c[a] = N[a] / 2.0f;
-                sa[a] = N[a] / float(M[a]);
-                const double sc = double(M[a]) / double(n3[a]);
-                V.sc_hi[a] = float(sc);
-                V.sc_lo[a] = float(sc - double(V.sc_hi[a]));
-            }
-            const float smin = fminf(sa[0], fminf(sa[1], sa[2]));
-            V.delta = w.step * smin;
-            bool ok32 = true;
-            for (int a = 0; a < 3; ++a) {
-                const double sc = double(M[a]) / double(n3[a]);
-                V.dU[a] = llrint(double(V.delta) * double(-V.b[a]) * sc * 4294967296.0);
-                const long long m = V.dU[a] < 0 ? -V.dU[a] : V.dU[a];
-                V.inv_m[a] = m ? float(1.0 / double(m)) : 0.0f;
-                const long long q = m ? (8LL << 32) / m : 0;
-                V.qq[a] = uint32_t(std::min<long long>(q, 1LL << 30));
-                V.rr[a] = uint32_t(m ? (8LL << 32) - q * m : 0);
-                if (m >= (1LL << 32)) ok32 = false;
-            }
-            V.skip_ok = ok32 ? 1 : 0;
-            V.L = L;
-            V.W = w.width;
-            V.H = w.height;
-            V.level = w.level;
-            V.tiles_w = (w.width + kTileW - 1) / kTileW;
+            fill_view(sm, w, V);
             V.out_offset = out_off;
             V.tile_begin = tiles;
             tiles += int64_t(V.tiles_w) * ((w.height + kTileH - 1) / kTileH);

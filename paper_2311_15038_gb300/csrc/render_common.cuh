@@ -1,0 +1,394 @@
+// render_common.cuh -- the per-ray part of slicemap rendering (Sec. III-C),
+// shared by the single-call renderer (render.cu) and the batched, work-queue
+// renderer (render_batch.cu), so both produce the same bits for a ray.
+//
+// Per ray:
+//  * set-up in FP32 with one rounding per operation in a fixed order (camera
+//    origin, slab intersection, sample count n = floor((t_far - t_near) /
+//    Delta)), so n matches any other IEEE implementation of the same steps;
+//  * the level coordinate of sample k is q0 + k dq, held as 32.32 fixed-point
+//    integers: dq once per view on the host (FP64), q0 once per ray in
+//    float-float arithmetic (no FP64, which runs at a small fraction of the
+//    FP32 rate on this part), so stepping is exact integer arithmetic and a
+//    sample position is accurate to ~1e-9 voxel;
+//  * trilinear interpolation of the atlas in FP32 (corner indices clamped to
+//    the level), transfer-function lookup with linear interpolation,
+//    premultiplied over-compositing, exit once A >= alpha_stop.
+//
+// Empty-space skipping: given a bitmap of the 8^3 cells whose maximum (over
+// the cell plus one voxel, i.e. every voxel a sample with its lower corner in
+// the cell reads) can produce a nonzero opacity under the transfer function,
+// a sample whose lower corner lies in an unmarked cell has opacity exactly 0
+// and adds exactly nothing to C and A.  An exact integer DDA over the cells
+// gives the index of the first sample of the next cell and the march jumps
+// there, so images and sample counts equal those of a full march.
+#pragma once
+
+#include <math.h>
+
+#include <algorithm>
+
+#include "mctp_internal.cuh"
+
+namespace mctp {
+namespace render {
+
+constexpr int kMaxLut = 4096;
+
+// Per-view constants of the march (computed on the host by fill_view).
+struct ViewParams {
+    float b[3], r[3], u[3];
+    float c[3], N[3];
+    float L, delta;
+    int32_t W, H;
+    int32_t tiles_w;  // 16 x 16 image tiles along x (single-call renderer)
+    int32_t level;
+    float sc_hi[3], sc_lo[3];  // M_a / N_a as an unevaluated float sum
+    float inv_m[3];            // 1 / |dU| (0 when dU == 0)
+    long long dU[3];           // fixed-point step of the level coordinate per sample
+    uint32_t qq[3], rr[3];     // 8 voxels (fixed point) = qq |dU| + rr (qq capped at 2^30)
+    int32_t skip_ok;           // |dU| < 2^32 on every axis: the cell DDA runs in 32 bits
+    int64_t out_offset;        // in floats
+    int64_t tile_begin;        // first tile of this view (single-call renderer)
+};
+
+// Level geometry of the march.
+struct LevelGeom {
+    int32_t m1[3];   // M_a - 1
+    uint32_t pitch;  // elements per atlas row
+    int32_t gy;      // bitmap: cells along y
+    int32_t wpr;     // bitmap: 32-bit words per (cz, cy) row
+};
+
+template <typename T>
+__device__ __forceinline__ float texel(const T *atlas, uint32_t off)
+{
+    return float(__ldg(atlas + off));
+}
+
+// Error-free transformations (Knuth's TwoSum; the FMA TwoProduct): a + b and
+// a * b as an unevaluated sum hi + lo of two floats.
+__device__ __forceinline__ void two_sum(float a, float b, float &hi, float &lo)
+{
+    hi = __fadd_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &hi, float &lo)
+{
+    hi = __fmul_rn(a, b);
+    lo = fmaf(a, b, -hi);
+}
+
+// Fixed-point (32.32) level coordinate (o + t0 d) * sc - 1/2 of a ray's first
+// sample, t0 = tn + h, in float-float arithmetic (relative error ~2^-44).
+__device__ __forceinline__ long long start_coord(float o, float d, float tn, float h, float sc_hi, float sc_lo)
+{
+    float t_hi, t_lo, p_hi, p_lo, s_hi, s_lo, m_hi, m_lo;
+    two_sum(tn, h, t_hi, t_lo);
+    two_prod(t_hi, d, p_hi, p_lo);
+    p_lo = fmaf(t_lo, d, p_lo);
+    two_sum(o, p_hi, s_hi, s_lo);
+    s_lo = __fadd_rn(s_lo, p_lo);
+    two_prod(s_hi, sc_hi, m_hi, m_lo);
+    m_lo = fmaf(s_hi, sc_lo, fmaf(s_lo, sc_hi, m_lo));
+    return __float2ll_rn(__fmul_rn(m_hi, 4294967296.0f)) + __float2ll_rn(__fmul_rn(m_lo, 4294967296.0f)) -
+           (1LL << 31);
+}
+
+// Lookup coordinate of a raw interpolated value, as the march computes it.
+__device__ __forceinline__ float lut_coord(float raw, float inv_vmax, float nl1)
+{
+    return __fmul_rn(fminf(__fmul_rn(raw, inv_vmax), 1.0f), nl1);
+}
+
+// Largest raw grey value S such that every sample whose corners are all <= S
+// has opacity exactly 0 under a transfer function whose entries 0..zmax (and
+// no more) have zero opacity; -1 when none.  Corners <= S give an
+// interpolated value below S + 1, whose lookup coordinate is <= that of
+// S + 1; if that coordinate is <= zmax the interpolated opacity is exactly 0.
+// All-zero corners interpolate to exactly 0, which is enough when entry 0 is
+// zero.
+__device__ inline int skip_threshold_from(int zmax, int nlut, float inv_vmax, int vmax_int)
+{
+    if (zmax < 0) return -1;
+    const float nl1 = float(nlut - 1), zf = float(zmax);
+    int lo = -1, hi = vmax_int;  // invariant: lo satisfies (or is -1), hi + 1 fails or hi is the top
+    if (lut_coord(float(vmax_int) + 1.0f, inv_vmax, nl1) <= zf) return vmax_int;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (lut_coord(float(mid) + 1.0f, inv_vmax, nl1) <= zf) lo = mid;
+        else hi = mid;
+    }
+    return lo > 0 ? lo : 0;
+}
+
+// skip_threshold_from for the transfer function `lut` (scanned serially).
+__device__ inline int skip_threshold(const float4 *lut, int nlut, float inv_vmax, int vmax_int)
+{
+    int zmax = -1;
+    while (zmax + 1 < nlut && lut[zmax + 1].w == 0.0f) ++zmax;
+    return skip_threshold_from(zmax, nlut, inv_vmax, vmax_int);
+}
+
+// Bitmap word w (rows of wpr words per (cz, cy)) of the cells whose maximum
+// exceeds S, from a max grid of gx cells per row.
+__device__ __forceinline__ uint32_t occupancy_word(const uint16_t *maxgrid, int gx, int wpr, int w, int S)
+{
+    const int r = w / wpr, wx = w - r * wpr;
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+        const int cx = wx * 32 + b;
+        if (cx < gx && int(__ldg(maxgrid + int64_t(r) * gx + cx)) > S) bits |= 1u << b;
+    }
+    return bits;
+}
+
+// Table access of the march: the transfer function, the atlas offset of each
+// slice and the cell bitmap, from shared memory or through the read-only
+// cache.
+struct SharedTables {
+    const float4 *lut;
+    const uint32_t *slice_off;
+    const uint32_t *occ;
+    __device__ __forceinline__ float4 lut_at(int j) const { return lut[j]; }
+    __device__ __forceinline__ uint32_t slice_at(int z) const { return slice_off[z]; }
+    __device__ __forceinline__ uint32_t occ_at(int w) const { return occ[w]; }
+};
+
+template <bool kLutShared>
+struct CachedTables {
+    const float4 *lut;
+    const uint32_t *slice_off;
+    const uint32_t *occ;
+    __device__ __forceinline__ float4 lut_at(int j) const { return kLutShared ? lut[j] : __ldg(lut + j); }
+    __device__ __forceinline__ uint32_t slice_at(int z) const { return __ldg(slice_off + z); }
+    __device__ __forceinline__ uint32_t occ_at(int w) const { return __ldg(occ + w); }
+};
+
+// March the ray of pixel (px, py) of view V through a level; returns the
+// premultiplied (C, A) and adds the number of samples taken to `taken`.
+template <typename T, class Tab>
+__device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas, const LevelGeom &G, bool use_skip,
+                                            const Tab &tab, int nlut, float inv_vmax, float alpha_stop, int px,
+                                            int py, unsigned long long &taken)
+{
+    // ---- FP32 ray set-up, one rounding per operation, fixed order
+    const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
+    const float sy = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn(float(py), 0.5f), float(V.H)));
+    const float sxL = __fmul_rn(sx, V.L), syL = __fmul_rn(sy, V.L);
+    float o[3], d[3];
+    float tmin = -INFINITY, tmax = INFINITY;
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float t1 = __fadd_rn(V.c[a], __fmul_rn(sxL, V.r[a]));
+        const float t2 = __fadd_rn(t1, __fmul_rn(syL, V.u[a]));
+        o[a] = __fadd_rn(t2, __fmul_rn(V.L, V.b[a]));
+        d[a] = -V.b[a];
+        if (d[a] != 0.0f) {
+            const float inv = __frcp_rn(d[a]);
+            const float s0 = __fmul_rn(__fsub_rn(0.0f, o[a]), inv);
+            const float s1 = __fmul_rn(__fsub_rn(V.N[a], o[a]), inv);
+            tmin = fmaxf(tmin, fminf(s0, s1));
+            tmax = fminf(tmax, fmaxf(s0, s1));
+        } else if (!(o[a] >= 0.0f && o[a] <= V.N[a])) {
+            miss = true;
+        }
+    }
+    int64_t n = 0;
+    if (!miss && tmax > tmin) n = int64_t(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
+    if (n <= 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // ---- fixed-point level coordinates of sample 0; the step is per view
+    long long U0[3];
+    const long long *dU = V.dU;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) U0[a] = start_coord(o[a], d[a], tmin, 0.5f * V.delta, V.sc_hi[a], V.sc_lo[a]);
+    const int *Mm1 = G.m1;
+    // ---- exact integer DDA over the 8^3 cells of each sample's lower corner:
+    // nxt[a] is the first sample index whose corner is in the next cell along
+    // axis a; with m = |dU| (< 2^32), D = 8 voxels, D = q m + r, the crossing
+    // after one at c (slack e = c m - distance, 0 <= e < m) is at
+    // c + q + (r > e), slack e + (r > e ? m : 0) - r.  Indices past the ray's
+    // end stand for "no further crossing".
+    const bool skip = use_skip && V.skip_ok;
+    constexpr int kInf = 0x7fffffff;
+    int cc[3], nxt[3];
+    uint32_t ee[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cc[a] = min(max(int(U0[a] >> 32), 0), Mm1[a]) >> 3;
+        nxt[a] = kInf;
+        ee[a] = 0;
+        const int last = Mm1[a] >> 3;
+        if (skip && dU[a] != 0 && (dU[a] > 0 ? cc[a] < last : cc[a] > 0)) {
+            const long long m = dU[a] > 0 ? dU[a] : -dU[a];
+            const long long num = dU[a] > 0 ? ((long long)(8 * cc[a] + 8) << 32) - U0[a]
+                                            : U0[a] - ((long long)(8 * cc[a]) << 32) + 1;
+            // c = ceil(num / m): float estimate, then exact correction
+            const float est = float(num) * V.inv_m[a];
+            if (est < float(n) + 2.0f) {
+                long long c = (long long)est;
+                while (c * m < num) ++c;
+                while (c > 0 && (c - 1) * m >= num) --c;
+                nxt[a] = int(c);
+                ee[a] = uint32_t(c * m - num);
+            }
+        }
+    }
+    auto cross = [&](int a) {
+        const bool fwd = dU[a] > 0;
+        cc[a] += fwd ? 1 : -1;
+        if (fwd ? cc[a] >= (Mm1[a] >> 3) : cc[a] <= 0) {
+            nxt[a] = kInf;  // the last cell this way: clamping keeps the corner in it
+            return;
+        }
+        const uint32_t m = uint32_t(fwd ? dU[a] : -dU[a]);
+        const bool up = V.rr[a] > ee[a];
+        nxt[a] = int(min(uint32_t(nxt[a]) + V.qq[a] + (up ? 1u : 0u), uint32_t(kInf)));
+        ee[a] += (up ? m : 0u) - V.rr[a];
+    };
+    auto marked = [&]() -> bool {
+        const uint32_t word = tab.occ_at((cc[2] * G.gy + cc[1]) * G.wpr + (cc[0] >> 5));
+        return (word >> (cc[0] & 31)) & 1u;
+    };
+    const uint32_t pitch = G.pitch;
+    const float nl1 = float(nlut - 1);
+    const int jmax = nlut - 2;
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+    int k = 0;
+    const int nn = int(n);
+    bool occupied = skip ? marked() : true;  // the current cell's bit, refreshed at every crossing
+    while (k < nn) {
+        if (!occupied) {
+            // an empty cell: its samples have opacity exactly 0; jump to the
+            // first sample of the next cell
+            const int kn = min(min(nxt[0], nxt[1]), nxt[2]);
+            if (kn >= nn) { k = nn; break; }
+            k = kn;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (nxt[a] == kn) cross(a);
+            occupied = marked();
+            continue;
+        }
+        long long U[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) U[a] = U0[a] + (long long)k * dU[a];
+        const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
+        const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]), z0i = min(max(iz, 0), Mm1[2]);
+        const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
+        const int z1i = min(max(iz + 1, 0), Mm1[2]);
+        const float fx = float(uint32_t(U[0])) * 2.3283064365386963e-10f;
+        const float fy = float(uint32_t(U[1])) * 2.3283064365386963e-10f;
+        const float fz = float(uint32_t(U[2])) * 2.3283064365386963e-10f;
+        const uint32_t za = tab.slice_at(z0i), zb = tab.slice_at(z1i);
+        const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
+        const float v000 = texel(atlas, za + ya + x0), v100 = texel(atlas, za + ya + x1);
+        const float v010 = texel(atlas, za + yb + x0), v110 = texel(atlas, za + yb + x1);
+        const float v001 = texel(atlas, zb + ya + x0), v101 = texel(atlas, zb + ya + x1);
+        const float v011 = texel(atlas, zb + yb + x0), v111 = texel(atlas, zb + yb + x1);
+        const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
+        const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
+        const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+        const float x = lut_coord(fmaf(fz, c1 - c0, c0), inv_vmax, nl1);
+        const int j = min(int(x), jmax);
+        const float fl = x - float(j);
+        const float4 e0 = tab.lut_at(j), e1 = tab.lut_at(j + 1);
+        const float ca = fmaf(fl, e1.w - e0.w, e0.w);
+        const float w = (1.0f - A) * ca;
+        C0 = fmaf(w, fmaf(fl, e1.x - e0.x, e0.x), C0);
+        C1 = fmaf(w, fmaf(fl, e1.y - e0.y, e0.y), C1);
+        C2 = fmaf(w, fmaf(fl, e1.z - e0.z, e0.z), C2);
+        A += w;
+        ++k;
+        if (A >= alpha_stop) break;
+        if (skip) {
+            bool moved = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (nxt[a] == k) { cross(a); moved = true; }
+            if (moved) occupied = marked();
+        }
+    }
+    taken += (unsigned long long)k;
+    return make_float4(C0, C1, C2, A);
+}
+
+// ---- host side
+
+constexpr int kTileW = 16, kTileH = 16;
+
+// Per-view constants of `w` on level w.level of `sm` (camera basis in FP64,
+// rounded once to float; fixed-point step and cell-DDA constants).
+inline void fill_view(const mctp_slicemap *sm, const mctp_view &w, ViewParams &V)
+{
+    const double PI = 3.14159265358979323846;
+    const int64_t n3[3] = {sm->src_dims[0], sm->src_dims[1], sm->src_dims[2]};
+    const float L = float(sqrt(double(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2])));
+    const float N[3] = {float(n3[0]), float(n3[1]), float(n3[2])};
+    const double az = (double(w.azimuth_deg) * PI) / 180.0;
+    const double el = (double(w.elevation_deg) * PI) / 180.0;
+    V.b[0] = float(cos(el) * cos(az));
+    V.b[1] = float(cos(el) * sin(az));
+    V.b[2] = float(sin(el));
+    V.r[0] = float(-sin(az));
+    V.r[1] = float(cos(az));
+    V.r[2] = 0.0f;
+    V.u[0] = float(-sin(el) * cos(az));
+    V.u[1] = float(-sin(el) * sin(az));
+    V.u[2] = float(cos(el));
+    const int *M = sm->dims[w.level];
+    float sa[3];
+    for (int a = 0; a < 3; ++a) {
+        V.N[a] = N[a];
+        V.c[a] = N[a] / 2.0f;
+        sa[a] = N[a] / float(M[a]);
+        const double sc = double(M[a]) / double(n3[a]);
+        V.sc_hi[a] = float(sc);
+        V.sc_lo[a] = float(sc - double(V.sc_hi[a]));
+    }
+    const float smin = fminf(sa[0], fminf(sa[1], sa[2]));
+    V.delta = w.step * smin;
+    bool ok32 = true;
+    for (int a = 0; a < 3; ++a) {
+        const double sc = double(M[a]) / double(n3[a]);
+        V.dU[a] = llrint(double(V.delta) * double(-V.b[a]) * sc * 4294967296.0);
+        const long long m = V.dU[a] < 0 ? -V.dU[a] : V.dU[a];
+        V.inv_m[a] = m ? float(1.0 / double(m)) : 0.0f;
+        const long long q = m ? (8LL << 32) / m : 0;
+        V.qq[a] = uint32_t(std::min<long long>(q, 1LL << 30));
+        V.rr[a] = uint32_t(m ? (8LL << 32) - q * m : 0);
+        if (m >= (1LL << 32)) ok32 = false;
+    }
+    V.skip_ok = ok32 ? 1 : 0;
+    V.L = L;
+    V.W = w.width;
+    V.H = w.height;
+    V.level = w.level;
+    V.tiles_w = (w.width + kTileW - 1) / kTileW;
+    V.out_offset = 0;
+    V.tile_begin = 0;
+}
+
+// Argument checks shared by the renderers: a view on level `w.level` of a
+// slicemap with `nlevels` levels.
+inline int check_view(const mctp_view &w, int nlevels)
+{
+    if (w.width < 1 || w.height < 1 || w.level < 0 || w.level >= nlevels) return MCTP_EINVAL;
+    if (!(w.step >= 1.0f / 256.0f && w.step <= 64.0f)) return MCTP_EINVAL;
+    if (int64_t(w.width) * w.height > (int64_t(1) << 28)) return MCTP_ESIZE;
+    return MCTP_OK;
+}
+
+// A level's atlas must be addressable with 32-bit texel offsets.
+inline bool level_fits_32bit(const mctp_slicemap *sm, int k)
+{
+    return int64_t(sm->tiles_x[k]) * sm->dims[k][0] * int64_t(sm->tiles_y[k]) * sm->dims[k][1] <=
+           (int64_t(1) << 32);
+}
+
+}  // namespace render
+}  // namespace mctp

@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(lib):
     from paper_2311_15038_gb300 import _lib
     names = _declared()
     assert {"mctp_build_histogram", "mctp_select_threshold", "mctp_filter_threshold", "mctp_build_slicemap",
-            "mctp_render_views"} <= names
+            "mctp_render_views", "mctp_render_batch", "mctp_render_batch_workspace"} <= names
     for n in sorted(names):
         assert hasattr(lib, n), n
         assert n in _lib.EXPORTS, f"{n} has no ctypes signature"
@@ -175,6 +175,70 @@ def test_render_rejects(lib):
     assert call(views=bad) == -1
     big = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 1 << 15, 1 << 14, 0, 0.5))
     assert call(views=big) == -3
+
+
+def _batch(lib, sms, views, vsm, vlut, nluts):
+    from paper_2311_15038_gb300 import _lib
+    S = (_lib.SlicemapDesc * len(sms))(*sms)
+    V = (_lib.ViewDesc * len(views))(*[_lib.ViewDesc(*v) for v in views])
+    A = (ctypes.c_int32 * len(vsm))(*vsm)
+    B = (ctypes.c_int32 * len(vlut))(*vlut)
+    return S, V, A, B
+
+
+def test_render_batch_workspace(lib):
+    s1 = _slicemap([(32, 32, 32), (16, 16, 16)])
+    s2 = _slicemap([(64, 48, 40)], src=(64, 48, 40), tiles=[(8, 5)])
+    s2.maxgrid[0] = 0x20000
+    nb = ctypes.c_size_t()
+
+    def size(views, vsm, vlut, nluts=2, sms=(s1, s2)):
+        S, V, A, B = _batch(lib, sms, views, vsm, vlut, nluts)
+        rc = lib.mctp_render_batch_workspace(S, len(sms), V, A, B, len(views), nluts, ctypes.byref(nb))
+        return rc, nb.value
+
+    one = (0.0, 0.0, 16, 16, 0, 0.5)
+    rc, base = size([one], [0], [0])
+    assert rc == 0 and base > 0 and base % 256 == 0
+    # a second view of the same (slicemap, level, LUT) adds only its record
+    rc, same = size([one, one], [0, 0], [0, 0])
+    assert rc == 0 and base <= same <= base + 512
+    # another LUT on a slicemap with a max grid adds slice offsets and a bitmap
+    rc, a = size([one, one], [1, 1], [0, 0])
+    rc2, b = size([one, one], [1, 1], [0, 1])
+    assert rc == rc2 == 0 and b >= a + 2 * 256
+    assert size([one], [2], [0])[0] == -1                    # slicemap index out of range
+    assert size([one], [0], [2])[0] == -1                    # LUT index out of range
+    assert size([(0.0, 0.0, 16, 16, 2, 0.5)], [0], [0])[0] == -1   # level out of range
+    s3 = _slicemap([(32, 32, 32)], dtype=2, bits=12)
+    assert size([one], [0], [0], sms=(s1, s3))[0] == -2      # one element type per batch
+
+
+def test_render_batch_rejects(lib):
+    from paper_2311_15038_gb300 import _lib
+    s1 = _slicemap([(32, 32, 32)])
+    S, V, A, B = _batch(lib, [s1], [(0.0, 0.0, 16, 16, 0, 0.5)], [0], [0], 1)
+    nb = ctypes.c_size_t()
+    assert lib.mctp_render_batch_workspace(S, 1, V, A, B, 1, 1, ctypes.byref(nb)) == 0
+    WS = ctypes.c_void_p(0x100000)
+    ok = dict(lut=FAKE, nluts=1, nlut=256, stop=0.99, tun=None, out=FAKE, ws=WS, wsb=nb.value)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        t = a["tun"]
+        return lib.mctp_render_batch(S, 1, V, A, B, 1, a["lut"], a["nluts"], a["nlut"], a["stop"],
+                                     ctypes.byref(t) if t is not None else None, a["out"], None, a["ws"],
+                                     a["wsb"], None)
+    assert call(wsb=nb.value - 1) == -3                      # workspace too small
+    assert call(ws=ctypes.c_void_p(0x100010)) == -1          # workspace not 256-byte aligned
+    assert call(ws=None) == -1
+    assert call(nlut=1) == -1
+    assert call(stop=0.0) == -1
+    assert call(lut=ctypes.c_void_p(0x10004)) == -1
+    assert call(out=None) == -1
+    for w, c, k in [(2, 1, 0), (64, 1, 0), (12, 1, 0), (8, 65, 0), (8, -1, 0), (8, 1, -1)]:
+        assert call(tun=_lib.BatchTuning(w, c, k, 0)) == -1
+    assert call(tun=_lib.BatchTuning(8, 2, 0, 1)) == -1      # reserved must be 0
 
 
 def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
