@@ -8,11 +8,13 @@
 // level k-1, rounded half up.
 //
 // One CTA owns a group of G = 2^f x 2^f level-0 rows (f = halvings fused into
-// the kernel, at most 2), so the source is read from HBM exactly once:
+// the kernel, at most 2; 4 x 4 rows when nothing is fused), so the source is
+// read from HBM exactly once:
 //  * accumulate: for each level-0 row, every thread owns 16-byte column
 //    vectors of the source rows of that row's (z, y) footprint and sums them
 //    in registers (8 loads in flight), then stores the column sums to a
-//    double-buffered shared row;
+//    double-buffered shared row; when a source row has fewer vectors than
+//    the CTA has threads, several level-0 rows are accumulated at once;
 //  * x-reduce: threads sum each output voxel's x-footprint from shared
 //    memory, divide, write the level-0 atlas row and keep the value in shared
 //    memory;
@@ -35,6 +37,8 @@ namespace {
 constexpr int kSmThreads = 256;
 constexpr int kSmUnroll = 8;
 constexpr int kMaxFused = 2;
+constexpr int kGroupUnfused = 4;
+constexpr int kMaxGroupRows = 16;  // (2^kMaxFused)^2 and kGroupUnfused^2
 
 template <typename T>
 struct L0Args {
@@ -42,6 +46,9 @@ struct L0Args {
     int64_t nx, ny, nz;
     int32_t mx, my, mz;
     int32_t fused;              // extra levels produced in-kernel (0..2)
+    int32_t group;              // a CTA owns group x group level-0 rows (z, y)
+    int32_t rows_per_pass;      // level-0 rows accumulated at once
+    int64_t cstride;            // column sums per shared row: nx rounded up to a multiple of 4
     T *atlas[kMaxFused + 1];
     int32_t tiles_x[kMaxFused + 1];
     int64_t pitch[kMaxFused + 1];  // atlas row pitch in elements
@@ -89,7 +96,9 @@ __device__ __forceinline__ void add_vector_u8_packed(const uint4 &q, uint32_t *a
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        uint32_t even = w[k] & 0x00ff00ffu, odd = (w[k] >> 8) & 0x00ff00ffu;
+        uint32_t even, odd;  // bytes 0,2 and 1,3 zero-extended to 16-bit lanes
+        asm("prmt.b32 %0, %1, 0, 0x4240;" : "=r"(even) : "r"(w[k]));
+        asm("prmt.b32 %0, %1, 0, 0x4341;" : "=r"(odd) : "r"(w[k]));
         if (kMode == 2) {
             even &= lane_sign_mask(even + k_fast);
             odd &= lane_sign_mask(odd + k_fast);
@@ -103,9 +112,9 @@ __device__ __forceinline__ void add_vector_u8_packed(const uint4 &q, uint32_t *a
 // vectors of the row and sums them over the footprint's source rows in
 // registers (aligned rows: 8 loads in flight; other rows: two loads per vector,
 // 4 rows in flight).
-template <typename T, int kMode, bool kPacked, bool kAligned>
+template <typename T, int kMode, bool kPacked, bool kAligned, bool kOne>
 __device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int zlo, int zhi, int ylo, int yhi,
-                                                   uint32_t *colsum, const uint8_t *lut, uint32_t lo)
+                                                   uint32_t *colsum, const uint8_t *lut, uint32_t lo, int64_t v0)
 {
     constexpr int E = 16 / sizeof(T);
     constexpr int NA = kPacked ? (sizeof(T) == 1 ? 8 : 4) : E;
@@ -119,7 +128,9 @@ __device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int zlo, 
     const int64_t slice_jump = (a.ny - wy + 1) * row_bytes;
     const char *first = reinterpret_cast<const char *>(a.vol) + (int64_t(zlo) * a.ny + ylo) * row_bytes;
     const uint32_t k_fast = (0x8000u - lo) * 0x00010001u, ovf_bits = ~((a.limit - 1u) * 0x00010001u);
-    for (int64_t v = threadIdx.x; v < V; v += blockDim.x) {
+    // kOne: this thread's single vector v0 (v0 < V); else vectors v0, v0 +
+    // blockDim.x, ...
+    for (int64_t v = v0; kOne || v < V; v += blockDim.x) {
         uint32_t acc[NA];
 #pragma unroll
         for (int e = 0; e < NA; ++e) acc[e] = 0u;
@@ -182,52 +193,86 @@ __device__ __forceinline__ void accumulate_row_vec(const L0Args<T> &a, int zlo, 
 #pragma unroll
             for (int e = 0; e < E; e += 4)
                 *reinterpret_cast<uint4 *>(dst + e) = make_uint4(sums[e], sums[e + 1], sums[e + 2], sums[e + 3]);
+        } else if (v * E + E <= a.nx) {
+#pragma unroll
+            for (int e = 0; e < E; e += 4)
+                *reinterpret_cast<uint4 *>(dst + e) = make_uint4(sums[e], sums[e + 1], sums[e + 2], sums[e + 3]);
         } else {
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (v * E + e < a.nx) dst[e] = sums[e];
         }
+        if (kOne) break;
     }
 }
 
-template <typename T, bool kVec, int kMode, bool kPacked>
+template <typename T, bool kVec, int kMode, bool kPacked, bool kMulti>
 __device__ void level0_group(const L0Args<T> &a, int Z0, int Y0, int gz, int gy, uint32_t *colsum, uint16_t *grp,
                              const int32_t *zb, const int32_t *yb, const int32_t *xb, const uint8_t *lut,
                              uint32_t lo)
 {
+    // per pass (double-buffered like the column sums): each row's footprint
+    // size R in (z, y) (0 for rows past the level) and its atlas row offset
+    __shared__ uint32_t row_R[2][kMaxGroupRows];
+    __shared__ int64_t row_off[2][kMaxGroupRows];
     const int G = gz * gy;
-    for (int g = 0; g < G; ++g) {
-        const int zz = g / gy, yy = g % gy;
-        const int zlo = zb[zz], zhi = zb[zz + 1], ylo = yb[yy], yhi = yb[yy + 1];
-        uint32_t *cs = colsum + (g & 1) * a.nx;
-        accumulate_row_vec<T, kMode, kPacked, kVec>(a, zlo, zhi, ylo, yhi, cs, lut, lo);
-        __syncthreads();
-        const uint32_t R = uint32_t((zhi - zlo) * (yhi - ylo));
-        T *row = atlas_ptr(a.atlas[0], a.pitch[0], a.tiles_x[0], a.mx, a.my, 0, Y0 + yy, Z0 + zz);
-        for (int x = threadIdx.x; x < a.mx; x += blockDim.x) {
-            const int xlo = xb[x], xhi = xb[x + 1];
-            uint32_t s = 0;
-            for (int i = xlo; i < xhi; ++i) s += cs[i];
-            const uint32_t cnt = uint32_t(xhi - xlo) * R;
-            const uint32_t val = (s + cnt / 2u) / cnt;
-            row[x] = (T)val;
-            if (grp) grp[g * a.mx + x] = uint16_t(val);
+    const int P = kMulti ? a.rows_per_pass : 1;
+    const int64_t V = (a.nx * int64_t(sizeof(T)) + 15) / 16;  // 16-byte vectors per source row
+    const int t = int(threadIdx.x);
+    int pass = 0;
+    for (int g0 = 0; g0 < G; g0 += P, ++pass) {
+        const int b = pass & 1;
+        uint32_t *buf = colsum + b * (int64_t(P) * a.cstride);
+        if (t < P && g0 + t < G) {
+            const int g = g0 + t, zz = g / gy, yy = g - zz * gy;
+            const bool in = Z0 + zz < a.mz && Y0 + yy < a.my;
+            row_R[b][t] = in ? uint32_t((zb[zz + 1] - zb[zz]) * (yb[yy + 1] - yb[yy])) : 0u;
+            row_off[b][t] = in ? atlas_ptr(a.atlas[0], a.pitch[0], a.tiles_x[0], a.mx, a.my, 0, Y0 + yy, Z0 + zz) -
+                                     a.atlas[0]
+                               : 0;
         }
-        // no barrier: the next row accumulates into the other buffer, and the
-        // barrier after it orders this row's reads before that buffer's reuse
+        // accumulate: one row with all threads striding over its vectors, or
+        // (kMulti) P rows at once, thread t on vector t % V of row g0 + t / V
+        const int j = kMulti ? int(t / V) : 0;
+        const int g = g0 + j;
+        const int zz = g / gy, yy = g - zz * gy;
+        if (j < P && g < G && Z0 + zz < a.mz && Y0 + yy < a.my)
+            accumulate_row_vec<T, kMode, kPacked, kVec, kMulti>(a, zb[zz], zb[zz + 1], yb[yy], yb[yy + 1],
+                                                                buf + int64_t(j) * a.cstride, lut, lo,
+                                                                kMulti ? t - int64_t(j) * V : int64_t(t));
+        __syncthreads();
+        // x-reduce: each thread takes output columns x and all rows of the pass
+        const int rows = min(P, G - g0);
+        for (int x = t; x < a.mx; x += blockDim.x) {
+            const int xlo = xb[x];
+            const uint32_t xw = uint32_t(xb[x + 1] - xlo);
+            for (int jj = 0; jj < rows; ++jj) {
+                const uint32_t R = row_R[b][jj];
+                if (R == 0) continue;  // past the level (ragged group)
+                const uint32_t *cs = buf + int64_t(jj) * a.cstride + xlo;
+                uint32_t sum = 0;
+                for (uint32_t k = 0; k < xw; ++k) sum += cs[k];
+                const uint32_t cnt = xw * R;
+                const uint32_t val = (sum + cnt / 2u) / cnt;
+                a.atlas[0][row_off[b][jj] + x] = (T)val;
+                if (grp) grp[(g0 + jj) * a.mx + x] = uint16_t(val);
+            }
+        }
+        // no barrier: the next pass accumulates into the other buffers, and the
+        // barrier after it orders this pass's reads before their reuse
     }
 }
 
-template <typename T, bool kVec>
+template <typename T, bool kVec, bool kMulti>
 __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T> a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    const int gz = 1 << a.fused, gy = 1 << a.fused;
-    const int ngy = a.my / gy;
+    const int gz = a.group, gy = a.group;
+    const int ngy = (a.my + gy - 1) / gy;
     const int Z0 = (blockIdx.x / ngy) * gz, Y0 = (blockIdx.x % ngy) * gy;
 
-    uint32_t *colsum = reinterpret_cast<uint32_t *>(smem);                     // 2 * nx
-    int32_t *xb = reinterpret_cast<int32_t *>(colsum + 2 * a.nx);              // mx + 1
+    uint32_t *colsum = reinterpret_cast<uint32_t *>(smem);                     // 2 * rows_per_pass * cstride
+    int32_t *xb = reinterpret_cast<int32_t *>(colsum + 2 * a.rows_per_pass * a.cstride);  // mx + 1
     int32_t *zb = xb + a.mx + 1;                                               // gz + 1 (this group)
     int32_t *yb = zb + gz + 1;                                                 // gy + 1
     uint16_t *grp = reinterpret_cast<uint16_t *>(yb + gy + 1);                 // gz*gy*mx (when fused)
@@ -235,8 +280,8 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
     uint8_t *lut = reinterpret_cast<uint8_t *>(grp1 + (a.fused > 1 ? (gz / 2) * (gy / 2) * (a.mx / 2) : 0));
 
     for (int i = threadIdx.x; i <= a.mx; i += blockDim.x) xb[i] = int32_t((int64_t(i) * a.nx) / a.mx);
-    for (int i = threadIdx.x; i <= gz; i += blockDim.x) zb[i] = int32_t((int64_t(Z0 + i) * a.nz) / a.mz);
-    for (int i = threadIdx.x; i <= gy; i += blockDim.x) yb[i] = int32_t((int64_t(Y0 + i) * a.ny) / a.my);
+    for (int i = threadIdx.x; i <= gz; i += blockDim.x) zb[i] = int32_t((int64_t(min(Z0 + i, a.mz)) * a.nz) / a.mz);
+    for (int i = threadIdx.x; i <= gy; i += blockDim.x) yb[i] = int32_t((int64_t(min(Y0 + i, a.my)) * a.ny) / a.my);
     __syncthreads();
 
     __shared__ int sh_keep[2];
@@ -244,11 +289,12 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
     const int mode = load_keep_table(a.keep, a.nbins, a.shift, a.limit, lut, sh_keep, int(threadIdx.x),
                                      int(blockDim.x), &lo, [] { __syncthreads(); });
     uint16_t *g0 = a.fused ? grp : nullptr;
-    if (mode == 0 && sizeof(T) == 1 && a.packed) level0_group<T, kVec, 0, true>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
-    else if (mode == 0) level0_group<T, kVec, 0, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
-    else if (mode == 1) level0_group<T, kVec, 1, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
-    else if (a.packed) level0_group<T, kVec, 2, true>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
-    else level0_group<T, kVec, 2, false>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    if (mode == 0 && sizeof(T) == 1 && a.packed)
+        level0_group<T, kVec, 0, true, kMulti>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else if (mode == 0) level0_group<T, kVec, 0, false, kMulti>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else if (mode == 1) level0_group<T, kVec, 1, false, kMulti>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else if (a.packed) level0_group<T, kVec, 2, true, kMulti>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
+    else level0_group<T, kVec, 2, false, kMulti>(a, Z0, Y0, gz, gy, colsum, g0, zb, yb, xb, lut, lo);
     if (!a.fused) return;
     __syncthreads();
 
@@ -408,21 +454,29 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
         a.nbins = keep ? nbins : 0;
         a.shift = keep ? bin_shift(d->bits, nbins) : 0;
         a.limit = 1u << d->bits;
-        const int gz = 1 << fused, gy = 1 << fused;
+        // groups of 2^f x 2^f rows when f levels are fused, else 4 x 4 rows
+        // (ragged at the level's edges)
+        a.group = fused ? (1 << fused) : kGroupUnfused;
+        const int gz = a.group, gy = a.group;
+        const int64_t V = (a.nx * int64_t(sizeof(T)) + 15) / 16;
+        a.rows_per_pass = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(gz) * gy, kSmThreads / V)));
         // two 16-bit lanes per word stay exact when a footprint's sum fits 16 bits
         const int64_t rmax = ((d->ny + a.my - 1) / a.my) * ((d->nz + a.mz - 1) / a.mz);
         a.packed = d->bits <= 15 && rmax * ((int64_t(1) << d->bits) - 1) < 65536;
-        size_t smem = size_t(2) * a.nx * 4 + size_t(a.mx + 1 + gz + 1 + gy + 1) * 4;
+        a.cstride = (a.nx + 3) & ~int64_t(3);
+        size_t smem = size_t(2) * a.rows_per_pass * a.cstride * 4 + size_t(a.mx + 1 + gz + 1 + gy + 1) * 4;
         if (fused) smem += size_t(gz) * gy * a.mx * 2;
         if (fused > 1) smem += size_t(gz / 2) * (gy / 2) * (a.mx / 2) * 2;
         smem += keep ? size_t(nbins) : 0;
         if (smem > 220 * 1024) return MCTP_EUNSUPPORTED;
         const bool vec = (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && ((a.nx * int64_t(sizeof(T))) & 15) == 0;
-        auto kern = vec ? slicemap_level0_kernel<T, true> : slicemap_level0_kernel<T, false>;
+        const bool multi = a.rows_per_pass > 1;
+        auto kern = vec ? (multi ? slicemap_level0_kernel<T, true, true> : slicemap_level0_kernel<T, true, false>)
+                        : (multi ? slicemap_level0_kernel<T, false, true> : slicemap_level0_kernel<T, false, false>);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
             return MCTP_ECUDA;
-        const int64_t blocks = int64_t(a.mz / gz) * (a.my / gy);
+        const int64_t blocks = int64_t((a.mz + gz - 1) / gz) * ((a.my + gy - 1) / gy);
         if (blocks > 0x7fffffff) return MCTP_EUNSUPPORTED;
         kern<<<unsigned(blocks), kSmThreads, smem, s>>>(a);
         rc = launch_status();

@@ -251,6 +251,30 @@ def test_slicemap_unaligned_rows(env, shape, bits, mode):
         _check_atlases(sm, oracle.slicemap(vol, bits, dims, keep_ref), oracle)
 
 
+@pytest.mark.parametrize("shape,dims,bits,mode", [
+    ((77, 41, 90), (38, 41, 45), 8, "otsu"),      # several level-0 rows per pass, ragged 4 x 4 groups
+    ((50, 61, 400), (64, 30, 25), 8, "topslab"),  # table lookup, unaligned 400-byte rows
+    ((33, 35, 96), (96, 35, 11), 8, None),        # aligned rows, identity in x and y
+    ((21, 30, 70), (33, 13, 7), 12, "otsu"),      # u16, ragged groups
+])
+def test_slicemap_single_level_groups(env, shape, dims, bits, mode):
+    # dims are (mx, my, mz); shape is (nz, ny, nx)
+    # one level (nothing fused): a CTA takes 4 x 4 level-0 rows, clipped at the
+    # level's edges, and accumulates as many rows at once as its threads cover
+    mctp, oracle, phantom, dev = env
+    nz, ny, nx = shape
+    vol = phantom.generate_cpu(phantom.VolumeSpec(nx, ny, nz, bits=bits, seed=nx * 7 + nz, n_ell=5))
+    nbins = 256 if bits == 8 else 4096
+    keep_ref = None
+    if mode == "topslab":
+        keep_ref = oracle.keep_topslab(oracle.histogram(vol, bits, nbins, 0, 3)[0], 1)
+    elif mode is not None:
+        keep_ref = oracle.keep_threshold(nbins, oracle.otsu(oracle.histogram(vol, bits, nbins)[0])[0])
+    sm = mctp.Slicemap.allocate((nx, ny, nz), dims, 1, torch.from_numpy(vol[:1, :1, :1]).dtype, bits, dev)
+    mctp.build_slicemap(up(vol, dev), bits, sm, up(keep_ref, dev) if keep_ref is not None else None)
+    _check_atlases(sm, oracle.slicemap(vol, bits, [dims], keep_ref), oracle)
+
+
 def test_slicemap_custom_tiles(env):
     mctp, oracle, phantom, dev = env
     vol = phantom.generate_cpu(phantom.VolumeSpec(64, 48, 52, bits=8, seed=12, n_ell=4))
