@@ -269,6 +269,35 @@ int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
                       const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
                       void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * mctp_render_batch without a workspace argument, for callers that cannot
+ * give the library device memory (a C host program with no device allocator,
+ * a serving loop that must not allocate once running).  The paper has no
+ * counterpart; this is a calling convention of this library.  The scratch is
+ * one fixed array of MCTP_BATCH_STATIC_SCRATCH bytes in the library's device
+ * memory per device, so this call allocates nothing.
+ *   Arguments, results and errors are those of mctp_render_batch; a batch
+ *   whose workspace (mctp_render_batch_workspace) exceeds
+ *   MCTP_BATCH_STATIC_SCRATCH bytes is rejected with MCTP_ESIZE before
+ *   anything is enqueued.
+ *   The first call with a device current looks up the scratch address on
+ *   that device (a host-side query, no allocation); make that first call
+ *   before any stream capture.
+ *   Nothing in the scratch needs to start at zero: every call rewrites what
+ *   it uses (the work counter is cleared by an in-stream memset).
+ *   All calls on one device share the one scratch: two calls whose work can
+ *   overlap on the device (different streams, or host threads without
+ *   ordering) race and give wrong images.  Issue them on one stream, or order
+ *   them with events.
+ */
+#define MCTP_BATCH_STATIC_SCRATCH (8u << 20)
+
+int mctp_render_batch_static(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
+                             const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,
+                             const float *luts_rgba, int32_t nluts, int32_t nlut, float alpha_stop,
+                             const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
+                             void *stream);
+
 /* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
  * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
 int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);

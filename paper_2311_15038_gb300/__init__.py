@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import MctpError  # noqa: F401
 
 __all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
-           "render_batch", "render_batch_workspace", "BatchTuning", "Slicemap", "View", "default_tiles",
+           "render_batch", "render_batch_workspace", "render_batch_static", "BatchTuning", "Slicemap", "View", "default_tiles",
            "atlas_bytes", "version", "MctpError"]
 
 _DTYPES = {torch.uint8: (_lib.MCTP_U8, 1), torch.uint16: (_lib.MCTP_U16, 2), torch.int16: (_lib.MCTP_U16, 2)}
@@ -298,3 +298,24 @@ def render_batch(slicemaps, views, view_slicemap, view_lut, luts: torch.Tensor, 
                                      luts.shape[1], alpha_stop, ctypes.byref(t), _ptr(out), _ptr(samples),
                                      _ptr(workspace), workspace.numel(), _stream(stream)), "mctp_render_batch")
     return out, samples, workspace
+
+
+def render_batch_static(slicemaps, views, view_slicemap, view_lut, luts: torch.Tensor, alpha_stop: float = 0.99,
+                        tuning: BatchTuning | None = None, out: torch.Tensor | None = None,
+                        samples: torch.Tensor | None = None, stream=None):
+    """render_batch with the library's fixed device scratch instead of a workspace (no allocation in the call;
+    calls that can overlap on the device must not be issued concurrently).  Returns (flat RGBA, samples)."""
+    luts = _luts3(luts)
+    a = _BatchArgs(slicemaps, views, view_slicemap, view_lut)
+    dev = luts.device
+    total = sum(v.width * v.height * 4 for v in views)
+    if out is None:
+        out = torch.empty(max(total, 4), dtype=torch.float32, device=dev)
+    if samples is None:
+        samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    t = (tuning or BatchTuning()).c()
+    _lib.check(_lib.load().mctp_render_batch_static(a.sms, a.nsm, a.views, a.vsm, a.vlut, a.n, _ptr(luts),
+                                                    luts.shape[0], luts.shape[1], alpha_stop, ctypes.byref(t),
+                                                    _ptr(out), _ptr(samples), _stream(stream)),
+               "mctp_render_batch_static")
+    return out, samples

@@ -21,6 +21,7 @@ MCTP_THR_TOPSLAB = 2
 MCTP_THR_EXPLICIT = 3
 
 MCTP_MAX_LEVELS = 8
+MCTP_BATCH_STATIC_SCRATCH = 8 << 20
 MCTP_MAXGRID_CELL = 8
 
 C_I32 = ctypes.c_int32
@@ -67,6 +68,9 @@ EXPORTS = {
     "mctp_render_batch": ([ctypes.POINTER(SlicemapDesc), C_I32, ctypes.POINTER(ViewDesc), C_VP, C_VP, C_I32,
                            C_VP, C_I32, C_I32, ctypes.c_float, ctypes.POINTER(BatchTuning), C_VP, C_VP, C_VP,
                            ctypes.c_size_t, C_VP], ctypes.c_int),
+    "mctp_render_batch_static": ([ctypes.POINTER(SlicemapDesc), C_I32, ctypes.POINTER(ViewDesc), C_VP, C_VP, C_I32,
+                                  C_VP, C_I32, C_I32, ctypes.c_float, ctypes.POINTER(BatchTuning), C_VP, C_VP, C_VP],
+                                 ctypes.c_int),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),

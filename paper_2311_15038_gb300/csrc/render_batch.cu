@@ -18,6 +18,7 @@
 // Every step is a kernel launch or a memset on the caller's stream, so a call
 // can be captured in a CUDA graph.
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -433,4 +434,57 @@ extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mc
     const uint64_t grid = std::min<uint64_t>(ctas_needed, uint64_t(per_sm) * uint64_t(num_sms()));
     kern<<<unsigned(grid), kBatchThreads, smem, s>>>(P);
     return launch_status();
+}
+
+// ---- batched rendering without a caller workspace
+//
+// Some callers cannot hand the library device memory for the workspace: a
+// plain C host program with no device allocator of its own, or a serving loop
+// that must never enter an allocator once it runs.  For them the scratch lives
+// in a fixed-size array of this module's device memory, created with the
+// module, so no call allocates.  Its address is looked up once per device, on
+// the first call made with that device current.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // MCTP_BATCH_STATIC_SCRATCH
+static_assert(kStaticScratchBytes == MCTP_BATCH_STATIC_SCRATCH, "header and library disagree");
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) uint8_t g_batch_scratch[kStaticScratchBytes];
+
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Address of g_batch_scratch on the current device (looked up once per device).
+int static_scratch(void **ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCTP_ECUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_batch_scratch) != cudaSuccess || !p) return MCTP_ECUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *ptr = g_scratch_ptr[dev];
+    return MCTP_OK;
+}
+
+}  // namespace
+
+extern "C" int mctp_render_batch_static(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
+                                        const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,
+                                        const float *luts_rgba, int32_t nluts, int32_t nlut, float alpha_stop,
+                                        const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
+                                        void *stream)
+{
+    size_t need = 0;
+    int rc = mctp_render_batch_workspace(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, &need);
+    if (rc != MCTP_OK) return rc;
+    if (need > kStaticScratchBytes) return MCTP_ESIZE;
+    void *scratch = nullptr;
+    rc = static_scratch(&scratch);
+    if (rc != MCTP_OK) return rc;
+    return mctp_render_batch(sms, nsm, views, view_slicemap, view_lut, nviews, luts_rgba, nluts, nlut, alpha_stop,
+                             tuning, out_rgba, samples_taken, scratch, kStaticScratchBytes, stream);
 }

@@ -31,7 +31,8 @@ def test_exports_every_declared_symbol(lib):
     from paper_2311_15038_gb300 import _lib
     names = _declared()
     assert {"mctp_build_histogram", "mctp_select_threshold", "mctp_filter_threshold", "mctp_build_slicemap",
-            "mctp_render_views", "mctp_render_batch", "mctp_render_batch_workspace"} <= names
+            "mctp_render_views", "mctp_render_batch", "mctp_render_batch_workspace",
+            "mctp_render_batch_static"} <= names
     for n in sorted(names):
         assert hasattr(lib, n), n
         assert n in _lib.EXPORTS, f"{n} has no ctypes signature"
@@ -239,6 +240,23 @@ def test_render_batch_rejects(lib):
     for w, c, k in [(2, 1, 0), (64, 1, 0), (12, 1, 0), (8, 65, 0), (8, -1, 0), (8, 1, -1)]:
         assert call(tun=_lib.BatchTuning(w, c, k, 0)) == -1
     assert call(tun=_lib.BatchTuning(8, 2, 0, 1)) == -1      # reserved must be 0
+
+
+def test_render_batch_static_rejects_oversized_batch(lib):
+    from paper_2311_15038_gb300 import _lib
+    # a 1600^3 level with a max grid needs a ~1.1 MiB cell bitmap per transfer
+    # function: eight of them exceed the fixed scratch and are refused on the host
+    big = _slicemap([(1600, 1600, 1600)], src=(1600, 1600, 1600), tiles=[(64, 25)])
+    big.maxgrid[0] = 0x20000
+    n = 8
+    views = [(0.0, 0.0, 16, 16, 0, 0.5)] * n
+    S, V, A, B = _batch(lib, [big], views, [0] * n, list(range(n)), n)
+    nb = ctypes.c_size_t()
+    assert lib.mctp_render_batch_workspace(S, 1, V, A, B, n, n, ctypes.byref(nb)) == 0
+    assert nb.value > _lib.MCTP_BATCH_STATIC_SCRATCH
+    assert lib.mctp_render_batch_static(S, 1, V, A, B, n, FAKE, n, 256, 0.99, None, FAKE, None, None) == -3
+    # bad arguments are refused as by mctp_render_batch
+    assert lib.mctp_render_batch_static(S, 1, V, A, B, n, FAKE, n - 1, 256, 0.99, None, FAKE, None, None) == -1
 
 
 def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
