@@ -9,13 +9,19 @@ steps.  The input (14.6 GB) is larger than L2, so no flush is needed between
 steps.  Multi-GPU runs are independent replicas (weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mctp|reference]
-                  [--workload full|mid|slab|small|batch]
+                  [--workload full|mid|slab|small|batch|serve]
 
 --workload batch: 64 u8 phantoms with axes ~ U{384..1024} (22 GB resident),
 each through histogram, Otsu and a 256^3 slicemap, then 12 views of each at
 512 x 512 in one persistent render launch, the whole pass replayed as one
 CUDA graph; the line also times the plain per-volume and per-view render
 launches on the same slicemaps.
+
+--workload serve: 200 resident u8 cubes (edge ~ U{256..1024}, 71 GB) with
+256^3 + 128^3 slicemaps; Poisson streams of preview requests (512^2 or
+1024^2, azimuth U[0, 360), elevation U[-60, 60], one of 8 transfer
+functions) at swept rates, served by the continuous-batching server and by
+one render_views launch per request; p50/p99 latency and samples/s per rate.
 """
 from __future__ import annotations
 
@@ -56,6 +62,13 @@ def workload(name: str):
                     az_step=10.0, desc="slab (profiling): u16 12-bit 2016x2016x224 phantom (1.8 GB) with the full "
                                        "workload's footprints, 4096 bins, Otsu, levels 512x512x64/256x256x32/"
                                        "128x128x16, 4 views 1024x1024")
+    if name == "serve":
+        specs = phantom.serve_specs(200)
+        return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=2, nviews=1,
+                    size=512, az_step=0.0, rates=(1000.0, 2500.0, 5000.0, 7500.0, 10000.0, 12500.0), requests=1500,
+                    desc="serve: 200 resident u8 cubes, edge ~U{256..1024} (%.1f GB), 256 bins, Otsu, slicemap "
+                         "levels 256^3/128^3, Poisson requests 512^2|1024^2, az U[0,360), el U[-60,60], LUT from "
+                         "8 presets, step 0.5, level 0" % (sum(sp.nbytes for sp in specs) / 1e9))
     if name == "batch":
         specs = phantom.batch_specs(64)
         return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=1, nviews=12,
@@ -621,13 +634,121 @@ def run_batch(args, wl):
     return 0
 
 
+def run_serve(args, wl):
+    """The serving workload: rate sweep, batched server against per-view launches."""
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    from paper_2311_15038_gb300 import serve as sv
+    mctp._lib.load()
+
+    vols, sms = [], []
+    for sp in wl["specs"]:
+        v = torch.empty(sp.shape, dtype=torch.uint8, device=dev)
+        phantom.generate_gpu(sp, v)
+        h, _ = mctp.build_histogram(v, 8, 256)
+        keep, _ = mctp.select_threshold(h, 256)
+        sm = mctp.Slicemap.allocate((sp.nx, sp.ny, sp.nz), wl["level0"], wl["nlevels"], torch.uint8, 8, dev)
+        mctp.build_slicemap(v, 8, sm, keep)
+        vols.append(v)
+        sms.append(sm)
+    luts = torch.from_numpy(np.stack(phantom.preset_luts())).to(dev)
+    torch.cuda.synchronize(dev)
+    arena = 8 << 30
+    configs = {"per_view": dict(mode="per_view", max_batch_views=1, max_inflight=1),
+               "batched": dict(mode="batched", max_batch_views=64, max_inflight=2)}
+    results = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, cfg in configs.items():
+        srv = sv.Server(sms, luts, arena, **cfg)
+        try:
+            warm = sv.poisson_trace(2000.0, 200, len(sms), luts.shape[0], seed=99)
+            sv.run_trace(srv, warm)
+            per_rate = {}
+            for k, rate in enumerate(wl["rates"]):
+                trace = sv.poisson_trace(rate, wl["requests"], len(sms), luts.shape[0], seed=1 + k)
+                s0 = srv.stats()["samples"]
+                done = sv.run_trace(srv, trace)
+                s1 = srv.stats()["samples"]
+                lat = np.array([f.t_done - a for a, f, _ in done]) * 1e3
+                t_first = min(a for a, _, _ in done)
+                t_last = max(f.t_done for _, f, _ in done)
+                per_rate[rate] = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                                      samples_per_s=(s1 - s0) / (t_last - t_first),
+                                      requests_per_s=len(done) / (t_last - t_first))
+            st = srv.stats()
+            per_rate["launches"] = st["launches"]
+            per_rate["arena_high_water_bytes"] = st["arena_high_water"]
+            results[name] = per_rate
+        finally:
+            srv.close()
+    clk = clocks.stop()
+    # end to end: the batched server at the top rate with every image copied to pinned host memory
+    srv = sv.Server(sms, luts, arena, **configs["batched"])
+    try:
+        top = wl["rates"][-1]
+        trace = sv.poisson_trace(top, wl["requests"], len(sms), luts.shape[0], seed=77)
+        s0 = srv.stats()["samples"]
+        done = sv.run_trace(srv, trace, copy_to_host=True)
+        s1 = srv.stats()["samples"]
+        t_first = min(a for a, _, _ in done)
+        t_last = max(tc for _, _, tc in done)
+        e2e_lat = np.array([tc - a for a, _, tc in done]) * 1e3
+        d2h = sum(a.view.width * a.view.height * 16 for a in trace)
+        e2e = dict(value=(s1 - s0) / (t_last - t_first), unit=UNIT, h2d_bytes_per_step=0,
+                   d2h_bytes_per_step=d2h, p50_ms=float(np.percentile(e2e_lat, 50)),
+                   p99_ms=float(np.percentile(e2e_lat, 99)), requests=len(done))
+    finally:
+        srv.close()
+    if rank != 0:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+        return 0
+    top = wl["rates"][-1]
+    b, p = results["batched"][top], results["per_view"][top]
+    pk = peaks()
+    line = dict(
+        metric=METRIC, value=b["samples_per_s"] * ws, unit=UNIT, n_gpus=ws, steps=len(wl["rates"]),
+        warmup=1, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u8/f32",
+        data="synthetic",
+        config=dict(workload=wl["desc"], l2="resident slicemaps 3.8 GB > L2; requests read them in place",
+                    parallelism=f"replicas x{ws}", server=configs["batched"], baseline=configs["per_view"],
+                    requests_per_rate=wl["requests"], rates_per_s=list(wl["rates"])),
+        latency_ms=dict(p50=b["p50_ms"], p99=b["p99_ms"]),
+        per_view_latency_ms=dict(p50=p["p50_ms"], p99=p["p99_ms"]),
+        serving=results,
+        roofline=None,
+        gpu_launches=None,
+        clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
+        e2e=e2e,
+        peak_source=pk["source"],
+    )
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small", "batch"])
+    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small", "batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = workload(args.workload)
@@ -635,6 +756,8 @@ def main():
         return run_reference(args, wl)
     if args.workload == "batch":
         return run_batch(args, wl)
+    if args.workload == "serve":
+        return run_serve(args, wl)
     return run_gpu(args, wl)
 
 

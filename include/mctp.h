@@ -298,6 +298,70 @@ int mctp_render_batch_static(const mctp_slicemap *sms, int32_t nsm, const mctp_v
                              const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
                              void *stream);
 
+/*
+ * Serving (an extension of this library: the paper's server renders previews
+ * on request and streams them to clients, Sec. III-C).  A server keeps the
+ * given slicemaps and transfer functions (caller memory, kept alive until
+ * destroy) and renders requests as they arrive:
+ *   - requests are admitted in arrival order while their image fits in the
+ *     free part of `arena` (caller device memory, 256-byte aligned; the
+ *     server's per-stream counters and batch workspaces come first, the image
+ *     heap after them): admission by memory;
+ *   - MCTP_SERVE_BATCHED: a host thread packs admitted requests into batches
+ *     of up to max_batch_views and launches each as one mctp_render_batch
+ *     launch on a free stream (up to max_inflight streams); requests that
+ *     arrive while batches are on the device join the next batch, which
+ *     starts as soon as a stream is free (continuous batching);
+ *   - MCTP_SERVE_PER_VIEW: one mctp_render_views launch per request, in
+ *     arrival order (the plain per-view baseline);
+ *   - a request's image is bit-identical to rendering its view alone with
+ *     mctp_render_views (same march).
+ * Times are mctp_now() seconds (a monotonic host clock).  t_done is when the
+ * server thread observed the completion of the request's launch.
+ * Errors: create: MCTP_EINVAL (bad arguments), MCTP_EUNSUPPORTED (mixed
+ * dtypes), MCTP_ESIZE (arena smaller than the server's fixed part),
+ * MCTP_ECUDA; submit: MCTP_EINVAL (bad view or index), MCTP_ESIZE (image
+ * larger than the whole image heap).  A launch failure is reported in the
+ * request's result status.
+ */
+#define MCTP_SERVE_BATCHED 0
+#define MCTP_SERVE_PER_VIEW 1
+
+typedef struct mctp_server mctp_server; /* opaque */
+
+typedef struct {
+    int32_t mode;             /* MCTP_SERVE_BATCHED or MCTP_SERVE_PER_VIEW */
+    int32_t max_batch_views;  /* BATCHED: views per launch, 1..4096 */
+    int32_t max_inflight;     /* launches on the device at once (streams), 1..8 */
+    int32_t reserved;         /* must be 0 */
+    mctp_batch_tuning tuning; /* BATCHED: launch shape (zeros = defaults) */
+} mctp_serve_params;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;           /* MCTP_OK, or the error of the request's launch */
+    int32_t reserved;
+    float *image;             /* device [height][width][4], valid until release */
+    double t_submit, t_admit, t_launch, t_done;
+} mctp_serve_result;
+
+int mctp_server_create(const mctp_slicemap *sms, int32_t nsm, const float *luts_rgba, int32_t nluts,
+                       int32_t nlut, float alpha_stop, void *arena, size_t arena_bytes,
+                       const mctp_serve_params *params, mctp_server **server);
+/* Queue one request; thread-safe. */
+int mctp_server_submit(mctp_server *server, const mctp_view *view, int32_t slicemap, int32_t lut,
+                       uint64_t *ticket);
+/* Move up to max_results finished requests (in completion order) to results. */
+int mctp_server_poll(mctp_server *server, mctp_serve_result *results, int32_t max_results, int32_t *count);
+/* Return a finished request's image memory to the arena. */
+int mctp_server_release(mctp_server *server, uint64_t ticket);
+/* Samples marched, launches made and the image heap's high-water mark (bytes). */
+int mctp_server_stats(mctp_server *server, uint64_t *samples, uint64_t *launches, uint64_t *arena_high_water);
+/* Wait for launches in flight, drop requests not yet launched, free the server. */
+int mctp_server_destroy(mctp_server *server);
+/* Monotonic host clock, seconds. */
+double mctp_now(void);
+
 /* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
  * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
 int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);

@@ -22,6 +22,8 @@ MCTP_THR_EXPLICIT = 3
 
 MCTP_MAX_LEVELS = 8
 MCTP_BATCH_STATIC_SCRATCH = 8 << 20
+MCTP_SERVE_BATCHED = 0
+MCTP_SERVE_PER_VIEW = 1
 MCTP_MAXGRID_CELL = 8
 
 C_I32 = ctypes.c_int32
@@ -54,6 +56,17 @@ class BatchTuning(ctypes.Structure):
     _fields_ = [("warp_w", C_I32), ("chunk", C_I32), ("ctas_per_sm", C_I32), ("reserved", C_I32)]
 
 
+class ServeParams(ctypes.Structure):
+    _fields_ = [("mode", C_I32), ("max_batch_views", C_I32), ("max_inflight", C_I32), ("reserved", C_I32),
+                ("tuning", BatchTuning)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", C_I32), ("reserved", C_I32), ("image", C_VP),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 EXPORTS = {
     "mctp_build_histogram": ([C_VP, ctypes.POINTER(VolumeDesc), C_I64, C_I64, C_I32, C_VP, C_VP, C_VP],
                              ctypes.c_int),
@@ -71,6 +84,16 @@ EXPORTS = {
     "mctp_render_batch_static": ([ctypes.POINTER(SlicemapDesc), C_I32, ctypes.POINTER(ViewDesc), C_VP, C_VP, C_I32,
                                   C_VP, C_I32, C_I32, ctypes.c_float, ctypes.POINTER(BatchTuning), C_VP, C_VP, C_VP],
                                  ctypes.c_int),
+    "mctp_server_create": ([ctypes.POINTER(SlicemapDesc), C_I32, C_VP, C_I32, C_I32, ctypes.c_float, C_VP,
+                            ctypes.c_size_t, ctypes.POINTER(ServeParams), ctypes.POINTER(C_VP)], ctypes.c_int),
+    "mctp_server_submit": ([C_VP, ctypes.POINTER(ViewDesc), C_I32, C_I32, ctypes.POINTER(ctypes.c_uint64)],
+                           ctypes.c_int),
+    "mctp_server_poll": ([C_VP, ctypes.POINTER(ServeResult), C_I32, ctypes.POINTER(C_I32)], ctypes.c_int),
+    "mctp_server_release": ([C_VP, ctypes.c_uint64], ctypes.c_int),
+    "mctp_server_stats": ([C_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                           ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "mctp_server_destroy": ([C_VP], ctypes.c_int),
+    "mctp_now": ([], ctypes.c_double),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),

@@ -284,13 +284,15 @@ extern "C" int mctp_render_batch_workspace(const mctp_slicemap *sms, int32_t nsm
     return MCTP_OK;
 }
 
-extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
-                                 const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,
-                                 const float *luts_rgba, int32_t nluts, int32_t nlut, float alpha_stop,
-                                 const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
-                                 void *workspace, size_t workspace_bytes, void *stream)
+namespace mctp {
+
+// mctp_render_batch with optional per-view output offsets (in floats from
+// out_rgba, 16-byte aligned); NULL: the images follow one another.
+int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, const int32_t *view_slicemap,
+                      const int32_t *view_lut, int32_t nviews, const float *luts_rgba, int32_t nluts, int32_t nlut,
+                      float alpha_stop, const mctp_batch_tuning *tuning, float *out_rgba, const int64_t *out_offsets,
+                      uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s)
 {
-    using namespace mctp;
     using namespace mctp::render;
     Plan plan;
     int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, plan);
@@ -311,7 +313,9 @@ extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mc
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1))) return MCTP_EINVAL;
     if (workspace_bytes < plan.total) return MCTP_ESIZE;
 
-    cudaStream_t s = as_stream(stream);
+    if (out_offsets)
+        for (int i = 0; i < nviews; ++i)
+            if (out_offsets[i] < 0 || (out_offsets[i] & 3)) return MCTP_EINVAL;
     if (samples_taken && cudaMemsetAsync(samples_taken, 0, sizeof(uint64_t), s) != cudaSuccess) return MCTP_ECUDA;
     if (nviews == 0) return MCTP_OK;
     uint8_t *ws = static_cast<uint8_t *>(workspace);
@@ -378,7 +382,7 @@ extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mc
             const mctp_view &w = views[i];
             BatchView &B = recs[size_t(i)];
             fill_view(&sms[view_slicemap[i]], w, B.vp);
-            B.vp.out_offset = out_off;
+            B.vp.out_offset = out_offsets ? out_offsets[i] : out_off;
             B.pair = plan.view_pair[size_t(i)];
             B.stiles_x = (w.width + sw - 1) / sw;
             B.item_begin = uint32_t(items);
@@ -434,6 +438,40 @@ extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mc
     const uint64_t grid = std::min<uint64_t>(ctas_needed, uint64_t(per_sm) * uint64_t(num_sms()));
     kern<<<unsigned(grid), kBatchThreads, smem, s>>>(P);
     return launch_status();
+}
+
+// Upper bound of mctp_render_batch_workspace over every batch of at most
+// max_views views of these slicemaps.
+size_t batch_workspace_bound(const mctp_slicemap *sms, int32_t nsm, int32_t max_views)
+{
+    size_t per_pair = 0;
+    for (int i = 0; i < nsm; ++i)
+        for (int k = 0; k < sms[i].nlevels; ++k) {
+            const int c = MCTP_MAXGRID_CELL;
+            size_t t = align_up(size_t(sms[i].dims[k][2]) * sizeof(uint32_t));
+            if (sms[i].maxgrid[k]) {
+                const size_t wpr = ((size_t(sms[i].dims[k][0]) + c - 1) / c + 31) / 32;
+                const size_t rows = ((size_t(sms[i].dims[k][1]) + c - 1) / c) * ((size_t(sms[i].dims[k][2]) + c - 1) / c);
+                t += align_up(rows * wpr * sizeof(uint32_t));
+            }
+            per_pair = std::max(per_pair, t);
+        }
+    const size_t v = size_t(std::max(max_views, 0));
+    return kAlign + align_up(v * sizeof(BatchView)) + align_up((v + 1) * sizeof(uint32_t)) +
+           align_up(v * sizeof(BatchPair)) + v * per_pair;
+}
+
+}  // namespace mctp
+
+extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
+                                 const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,
+                                 const float *luts_rgba, int32_t nluts, int32_t nlut, float alpha_stop,
+                                 const mctp_batch_tuning *tuning, float *out_rgba, uint64_t *samples_taken,
+                                 void *workspace, size_t workspace_bytes, void *stream)
+{
+    return mctp::render_batch_impl(sms, nsm, views, view_slicemap, view_lut, nviews, luts_rgba, nluts, nlut,
+                                   alpha_stop, tuning, out_rgba, nullptr, samples_taken, workspace, workspace_bytes,
+                                   mctp::as_stream(stream));
 }
 
 // ---- batched rendering without a caller workspace

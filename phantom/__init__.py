@@ -116,6 +116,16 @@ def batch_specs(count: int = 64, lo: int = 384, hi: int = 1024, seed: int = 3) -
     return out
 
 
+def serve_specs(count: int = 200, lo: int = 256, hi: int = 1024, seed: int = 5) -> list[VolumeSpec]:
+    """Resident u8 cubes for the serving workload: edge ~ U{lo..hi}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for j in range(count):
+        e = int(rng.integers(lo, hi + 1))
+        out.append(VolumeSpec(e, e, e, bits=8, seed=1000 * seed + j, n_ell=12, n_cyl=0))
+    return out
+
+
 def make_params(spec: VolumeSpec) -> ctypes.Array:
     lib = _cpu()
     buf = (ctypes.c_uint8 * lib.ph_params_size())()

@@ -259,6 +259,43 @@ def test_render_batch_static_rejects_oversized_batch(lib):
     assert lib.mctp_render_batch_static(S, 1, V, A, B, n, FAKE, n - 1, 256, 0.99, None, FAKE, None, None) == -1
 
 
+def test_server_rejects(lib):
+    from paper_2311_15038_gb300 import _lib
+    s1 = _slicemap([(32, 32, 32)])
+    S = (_lib.SlicemapDesc * 1)(s1)
+    out = ctypes.c_void_p()
+    ARENA = ctypes.c_void_p(0x1000000)
+
+    def create(mode=0, views=64, inflight=2, reserved=0, arena=ARENA, nbytes=1 << 30, nlut=256, stop=0.99,
+               sms=S, nsm=1, handle=True):
+        p = _lib.ServeParams(mode, views, inflight, reserved, _lib.BatchTuning(0, 0, 0, 0))
+        return lib.mctp_server_create(sms, nsm, FAKE, 1, nlut, stop, arena, nbytes, ctypes.byref(p),
+                                      ctypes.byref(out) if handle else None)
+    assert create(handle=False) == -1
+    assert create(mode=2) == -1
+    assert create(inflight=0) == -1
+    assert create(inflight=9) == -1
+    assert create(views=0) == -1
+    assert create(views=5000) == -1
+    assert create(reserved=1) == -1
+    assert create(arena=ctypes.c_void_p(0x1000010)) == -1    # arena not 256-byte aligned
+    assert create(nlut=1) == -1
+    assert create(stop=0.0) == -1
+    assert create(nbytes=4096) == -3                          # smaller than counters + batch workspaces
+    s3 = _slicemap([(32, 32, 32)], dtype=2, bits=12)
+    assert create(sms=(_lib.SlicemapDesc * 2)(s1, s3), nsm=2) == -2
+    # calls on no server
+    tk = ctypes.c_uint64()
+    v = _lib.ViewDesc(0.0, 0.0, 8, 8, 0, 0.5)
+    n = ctypes.c_int32()
+    assert lib.mctp_server_submit(None, ctypes.byref(v), 0, 0, ctypes.byref(tk)) == -1
+    assert lib.mctp_server_poll(None, None, 0, ctypes.byref(n)) == -1
+    assert lib.mctp_server_release(None, 1) == -1
+    assert lib.mctp_server_stats(None, None, None, None) == -1
+    assert lib.mctp_server_destroy(None) == -1
+    assert lib.mctp_now() > 0.0
+
+
 def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
     from paper_2311_15038_gb300 import _lib, build
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))

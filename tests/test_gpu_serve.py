@@ -1,0 +1,122 @@
+"""The preview server (mctp_server_*): requests submitted in bursts are
+batched, admitted by free arena memory and rendered on several streams.
+Every served image (and the server's sample total) must equal rendering the
+request's view alone with mctp_render_views: the same result alone and in
+the mix, bit for bit (so within the 2e-4 tolerance of the path)."""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    from paper_2311_15038_gb300 import serve
+    dev = torch.device("cuda:0")
+    V = phantom.VolumeSpec
+    specs = [(V(64, 64, 64, bits=8, seed=71, n_ell=5), [(32, 32, 32), (16, 16, 16)]),
+             (V(96, 80, 72, bits=8, seed=72, n_ell=6), [(48, 40, 36)]),
+             (V(50, 70, 90, bits=8, seed=73, n_ell=4), [(50, 70, 90), (25, 35, 45)])]
+    sms = []
+    for spec, dims in specs:
+        vol = torch.empty(spec.shape, dtype=torch.uint8, device=dev)
+        phantom.generate_gpu(spec, vol)
+        h, _ = mctp.build_histogram(vol, 8, 256)
+        keep, _ = mctp.select_threshold(h, 256)
+        sm = mctp.Slicemap.allocate((spec.nx, spec.ny, spec.nz), dims[0], len(dims), torch.uint8, 8, dev)
+        mctp.build_slicemap(vol, 8, sm, keep)
+        sms.append(sm)
+    luts = torch.from_numpy(np.stack(phantom.preset_luts())).to(dev)
+    return mctp, serve, sms, luts, dev
+
+
+def _requests(mctp, sms, n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        s = int(rng.integers(len(sms)))
+        w, h = [(48, 48), (64, 40), (17, 90), (96, 96), (1, 1)][i % 5]
+        v = mctp.View(float(rng.uniform(0, 360)), float(rng.uniform(-60, 60)), w, h,
+                      int(rng.integers(len(sms[s].dims))), 0.5)
+        out.append((v, s, int(rng.integers(8))))
+    return out
+
+
+def _alone(mctp, sms, luts, req):
+    v, s, l = req
+    flat, smp = mctp.render_views(sms[s], [v], luts[l], 0.99)
+    return flat[:v.width * v.height * 4].view(v.height, v.width, 4), int(smp.item())
+
+
+def _serve_all(srv, reqs, release=True, timeout=60.0):
+    tickets = {srv.submit(v, s, l): i for i, (v, s, l) in enumerate(reqs)}
+    got = {}
+    t0 = time.time()
+    while len(got) < len(reqs):
+        for f in srv.poll():
+            assert f.status == 0
+            got[tickets[f.ticket]] = (f, srv.image(f))
+            if release:
+                srv.release(f.ticket)
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.0005)
+    return got
+
+
+@pytest.mark.parametrize("mode,batch,inflight", [("batched", 16, 2), ("batched", 64, 4), ("per_view", 1, 1)])
+def test_served_equals_alone(env, mode, batch, inflight):
+    mctp, serve, sms, luts, dev = env
+    reqs = _requests(mctp, sms, 80, seed=5)
+    with serve.Server(sms, luts, 256 << 20, mode, batch, inflight) as srv:
+        got = _serve_all(srv, reqs)
+        st = srv.stats()
+    total = 0
+    for i, req in enumerate(reqs):
+        ref, smp = _alone(mctp, sms, luts, req)
+        total += smp
+        f, img = got[i]
+        assert torch.equal(img, ref), f"request {i} differs from rendering it alone"
+        assert f.t_submit <= f.t_admit <= f.t_launch <= f.t_done
+    assert st["samples"] == total
+    if mode == "batched":
+        assert st["launches"] < len(reqs)  # the burst was batched
+    else:
+        assert st["launches"] == len(reqs)
+
+
+def test_admission_by_memory(env):
+    """A 1 MiB arena whose image heap holds about six 96x96 images at a time:
+    requests wait for memory that releases free, and all of them still finish
+    with the right images."""
+    mctp, serve, sms, luts, dev = env
+    reqs = [(mctp.View(10.0 * i, 15.0, 96, 96, 0, 0.5), i % 3, i % 8) for i in range(24)]
+    img = 96 * 96 * 16
+    with serve.Server(sms, luts, 1 << 20, "batched", 8, 2) as srv:
+        got = _serve_all(srv, reqs)
+        st = srv.stats()
+    assert st["arena_high_water"] <= (1 << 20)
+    waited = sum(1 for f, _ in got.values() if f.t_admit > f.t_submit + 1e-4)
+    assert waited > 0, "no request had to wait for memory"
+    for i, req in enumerate(reqs):
+        ref, _ = _alone(mctp, sms, luts, req)
+        assert torch.equal(got[i][1], ref)
+    assert st["arena_high_water"] >= img
+
+
+def test_submit_rejects_image_larger_than_heap(env):
+    mctp, serve, sms, luts, dev = env
+    with serve.Server(sms, luts, 1 << 20, "batched", 8, 2) as srv:
+        with pytest.raises(mctp.MctpError):
+            srv.submit(mctp.View(0.0, 0.0, 512, 512, 0, 0.5), 0, 0)
+        with pytest.raises(mctp.MctpError):
+            srv.submit(mctp.View(0.0, 0.0, 8, 8, 5, 0.5), 0, 0)  # level out of range
