@@ -59,9 +59,13 @@ def _L():
                                                      C_VP, C_VP, C_VP, C_VP, C_VP]
         lib.orc_entropy.argtypes = [C_VP, ctypes.c_int, C_VP]
         lib.orc_maxgrid.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, ctypes.c_int, C_VP]
+        lib.orc_render_dense.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
+                                                               ctypes.POINTER(View), C_VP, C_I64, C_VP, C_VP]
+        lib.orc_render_dense_grad.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
+                                                                    ctypes.POINTER(View), C_VP, C_VP, C_VP]
         for f in ("orc_histogram", "orc_otsu", "orc_its", "orc_keep_threshold", "orc_keep_topslab",
                   "orc_filter", "orc_downsample", "orc_atlas_pack", "orc_render", "orc_ray_params",
-                  "orc_entropy", "orc_maxgrid"):
+                  "orc_entropy", "orc_maxgrid", "orc_render_dense", "orc_render_dense_grad"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -235,3 +239,41 @@ def maxgrid(level: np.ndarray, cell: int = 8) -> np.ndarray:
     g = np.zeros((-(-mz // cell), -(-my // cell), -(-mx // cell)), np.uint16)
     _check(_L().orc_maxgrid(_p(level), level.itemsize, mx, my, mz, cell, _p(g)), "maxgrid")
     return g
+
+
+def render_dense(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el: float, width: int, height: int,
+                 step: float = 0.5, alpha_stop: float = 0.99, pixels: np.ndarray | None = None):
+    """FP64 render of a dense intensity volume [z][y][x] -> (rgba [H][W][4] or [n][4], samples)."""
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    mz, my, mx = vol.shape
+    nx, ny, nz = src_dims
+    lut = np.ascontiguousarray(lut, dtype=np.float64)
+    v = View(az, el, width, height, step)
+    if pixels is None:
+        npix, pp = width * height, None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+        npix, pp = pixels.size, _p(pixels)
+    rgba = np.zeros((npix, 4), np.float64)
+    ns = np.zeros(npix, np.uint64)
+    _check(_L().orc_render_dense(_p(vol), mx, my, mz, nx, ny, nz, _p(lut), lut.shape[0], alpha_stop,
+                                 ctypes.byref(v), pp, npix, _p(rgba), _p(ns)), "render_dense")
+    if pixels is None:
+        return rgba.reshape(height, width, 4), ns.reshape(height, width)
+    return rgba, ns
+
+
+def render_dense_grad(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el: float, width: int,
+                      height: int, g_rgba: np.ndarray, step: float = 0.5, alpha_stop: float = 0.99):
+    """Gradient of sum(g_rgba * render_dense(...)) -> (g_vol like vol, g_lut like lut), FP64."""
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    mz, my, mx = vol.shape
+    nx, ny, nz = src_dims
+    lut = np.ascontiguousarray(lut, dtype=np.float64)
+    g = np.ascontiguousarray(g_rgba, dtype=np.float64).reshape(height * width * 4)
+    gv = np.zeros_like(vol)
+    gl = np.zeros_like(lut)
+    v = View(az, el, width, height, step)
+    _check(_L().orc_render_dense_grad(_p(vol), mx, my, mz, nx, ny, nz, _p(lut), lut.shape[0], alpha_stop,
+                                      ctypes.byref(v), _p(g), _p(gv), _p(gl)), "render_dense_grad")
+    return gv, gl

@@ -28,11 +28,16 @@
  *   orc_render      Beer-Lambert slab closed form, axis-aligned views against a
  *                   product-form compositor over scipy map_coordinates samples,
  *                   empty volume, axis-aligned sample counts
+ *   orc_render_dense      orc_render on the same level (intensities = raw/255),
+ *                         Beer-Lambert slab
+ *   orc_render_dense_grad central finite differences of orc_render_dense along
+ *                         random directions; closed-form dA/dalpha of a slab
  * No function here is "parity unpinned".
  */
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #define ORC_OK 0
@@ -597,4 +602,224 @@ int orc_entropy(const uint64_t *counts, int m, double *H_out)
             }
     *H_out = H;
     return ORC_OK;
+}
+
+/* ------------------------------------------- differentiable dense render */
+
+/*
+ * Rendering of a dense FP64 volume of intensities (the reduced volume that is
+ * fitted so that its renders match renders of the full-resolution source,
+ * the reduction goal of the previews, Sec. I / Sec. III).  Geometry, sample
+ * positions, trilinear interpolation, the transfer-function lookup and the
+ * compositing are those of orc_render, with the raw value already an
+ * intensity: v = min(max(raw, 0), 1); vol is [mz][my][mx], lut is double
+ * [nlut][4] (straight colour).  rgba gets the premultiplied (C, A) of every
+ * listed pixel (all pixels when pixels is NULL), nsamp the samples taken.
+ */
+typedef struct {
+    int64_t idx[8];  /* corner voxel indices (clamped), order (x,y,z) bits 0,1,2 */
+    double w[8];     /* trilinear weights */
+    double raw;      /* interpolated value before the clamp */
+} orc_tap;
+
+static void dense_tap(const double *vol, const int64_t M[3], const double q[3], orc_tap *tp)
+{
+    int64_t i0[3], i1[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(q[a]);
+        f[a] = q[a] - fl;
+        i0[a] = clampi((int64_t)fl, 0, M[a] - 1);
+        i1[a] = clampi((int64_t)fl + 1, 0, M[a] - 1);
+    }
+    double raw = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int64_t x = (c & 1) ? i1[0] : i0[0], y = (c & 2) ? i1[1] : i0[1], z = (c & 4) ? i1[2] : i0[2];
+        double w = ((c & 1) ? f[0] : 1.0 - f[0]) * ((c & 2) ? f[1] : 1.0 - f[1]) * ((c & 4) ? f[2] : 1.0 - f[2]);
+        tp->idx[c] = (z * M[1] + y) * M[0] + x;
+        tp->w[c] = w;
+        raw += w * vol[tp->idx[c]];
+    }
+    tp->raw = raw;
+}
+
+typedef struct {
+    double b[3];
+    float bf[3], rf[3], uf[3], L, c[3], N[3], delta;
+} orc_cam;
+
+static void dense_camera(int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny, int64_t nz,
+                         const orc_view *view, orc_cam *cam)
+{
+    const double PI = 3.14159265358979323846;
+    double az = ((double)view->az_deg * PI) / 180.0;
+    double el = ((double)view->el_deg * PI) / 180.0;
+    cam->bf[0] = (float)(cos(el) * cos(az));
+    cam->bf[1] = (float)(cos(el) * sin(az));
+    cam->bf[2] = (float)sin(el);
+    cam->rf[0] = (float)(-sin(az));
+    cam->rf[1] = (float)cos(az);
+    cam->rf[2] = 0.0f;
+    cam->uf[0] = (float)(-sin(el) * cos(az));
+    cam->uf[1] = (float)(-sin(el) * sin(az));
+    cam->uf[2] = (float)cos(el);
+    cam->L = (float)sqrt((double)(nx * nx + ny * ny + nz * nz));
+    cam->N[0] = (float)nx;
+    cam->N[1] = (float)ny;
+    cam->N[2] = (float)nz;
+    for (int a = 0; a < 3; ++a) cam->c[a] = cam->N[a] / 2.0f;
+    float s[3] = {cam->N[0] / (float)mx, cam->N[1] / (float)my, cam->N[2] / (float)mz};
+    cam->delta = view->step * fminf(s[0], fminf(s[1], s[2]));
+}
+
+/* Transfer function at intensity v: rgba, entry j and fraction f. */
+static void dense_lookup(const double *lut, int nlut, double v, double rgba[4], int64_t *j, double *f)
+{
+    double x = v * (double)(nlut - 1);
+    int64_t jj = (int64_t)floor(x);
+    if (jj > nlut - 2) jj = nlut - 2;
+    double ff = x - (double)jj;
+    for (int ch = 0; ch < 4; ++ch) rgba[ch] = lut[jj * 4 + ch] * (1.0 - ff) + lut[(jj + 1) * 4 + ch] * ff;
+    *j = jj;
+    *f = ff;
+}
+
+static int dense_args_ok(const double *vol, int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny,
+                         int64_t nz, const double *lut, int nlut, const orc_view *view)
+{
+    if (!vol || !lut || !view || nlut < 2) return 0;
+    if (mx <= 0 || my <= 0 || mz <= 0 || nx <= 0 || ny <= 0 || nz <= 0) return 0;
+    if (view->width <= 0 || view->height <= 0 || !(view->step > 0.0f)) return 0;
+    return 1;
+}
+
+int orc_render_dense(const double *vol, int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny, int64_t nz,
+                     const double *lut, int nlut, double alpha_stop, const orc_view *view,
+                     const int64_t *pixels, int64_t npix, double *rgba, uint64_t *nsamp)
+{
+    if (!dense_args_ok(vol, mx, my, mz, nx, ny, nz, lut, nlut, view) || !rgba) return ORC_EINVAL;
+    orc_cam cam;
+    dense_camera(mx, my, mz, nx, ny, nz, view, &cam);
+    const int64_t M[3] = {mx, my, mz};
+    const double Nd[3] = {(double)nx, (double)ny, (double)nz};
+    const int64_t W = view->width, H = view->height;
+    const int64_t total = pixels ? npix : W * H;
+    for (int64_t p = 0; p < total; ++p) {
+        int64_t lin = pixels ? pixels[p] : p;
+        if (lin < 0 || lin >= W * H) return ORC_EINVAL;
+        orc_ray ray;
+        ray_setup(cam.bf, cam.rf, cam.uf, cam.L, cam.c, cam.N, cam.delta, view->width, view->height, lin % W,
+                  lin / W, &ray);
+        double C[3] = {0, 0, 0}, A = 0.0;
+        int64_t k = 0;
+        while (k < ray.n) {
+            double t = (double)ray.t_near + ((double)k + 0.5) * (double)ray.delta;
+            double q[3];
+            for (int a = 0; a < 3; ++a) q[a] = (((double)ray.o[a] + t * (double)ray.d[a]) * (double)M[a]) / Nd[a] - 0.5;
+            orc_tap tp;
+            dense_tap(vol, M, q, &tp);
+            double v = tp.raw < 0.0 ? 0.0 : (tp.raw > 1.0 ? 1.0 : tp.raw);
+            double e[4];
+            int64_t j;
+            double f;
+            dense_lookup(lut, nlut, v, e, &j, &f);
+            double w = (1.0 - A) * e[3];
+            C[0] += w * e[0];
+            C[1] += w * e[1];
+            C[2] += w * e[2];
+            A += w;
+            ++k;
+            if (A >= alpha_stop) break;
+        }
+        rgba[p * 4 + 0] = C[0];
+        rgba[p * 4 + 1] = C[1];
+        rgba[p * 4 + 2] = C[2];
+        rgba[p * 4 + 3] = A;
+        if (nsamp) nsamp[p] = (uint64_t)k;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Gradient of sum_p g_rgba[p] . rgba[p] of orc_render_dense with respect to
+ * the volume and the transfer function (accumulated into g_vol, g_lut).
+ * Reverse-mode differentiation of the compositing recurrence
+ *   w_k = (1 - A_k) alpha_k,  C_{k+1} = C_k + w_k c_k,  A_{k+1} = A_k + w_k,
+ * over each ray's stored list of samples (the stop index is held fixed):
+ * with adjoints gC (constant along the ray) and gA_{k+1},
+ *   gw = gC . c_k + gA_{k+1};   g c_k = gC w_k;   g alpha_k = gw (1 - A_k);
+ *   gA_k = gA_{k+1} - gw alpha_k.
+ * Then the lookup: g lut[j] += (1-f) g e, g lut[j+1] += f g e, and
+ * g v = (nlut-1) sum_ch g e_ch (lut[j+1]_ch - lut[j]_ch) inside 0 < raw < 1
+ * (0 where the clamp is active); g vol[corner] += w_corner g v.
+ */
+int orc_render_dense_grad(const double *vol, int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny,
+                          int64_t nz, const double *lut, int nlut, double alpha_stop, const orc_view *view,
+                          const double *g_rgba, double *g_vol, double *g_lut)
+{
+    if (!dense_args_ok(vol, mx, my, mz, nx, ny, nz, lut, nlut, view) || !g_rgba || !g_vol || !g_lut)
+        return ORC_EINVAL;
+    orc_cam cam;
+    dense_camera(mx, my, mz, nx, ny, nz, view, &cam);
+    const int64_t M[3] = {mx, my, mz};
+    const double Nd[3] = {(double)nx, (double)ny, (double)nz};
+    const int64_t W = view->width, H = view->height;
+    /* per-ray sample list: tap, A before the sample, rgba, j, f */
+    int64_t cap = 0;
+    orc_tap *taps = NULL;
+    double *Ak = NULL, *E = NULL, *F = NULL;
+    int64_t *J = NULL;
+    int rc = ORC_OK;
+    for (int64_t lin = 0; lin < W * H && rc == ORC_OK; ++lin) {
+        orc_ray ray;
+        ray_setup(cam.bf, cam.rf, cam.uf, cam.L, cam.c, cam.N, cam.delta, view->width, view->height, lin % W,
+                  lin / W, &ray);
+        if (ray.n > cap) {
+            cap = ray.n;
+            free(taps); free(Ak); free(E); free(F); free(J);
+            taps = (orc_tap *)malloc((size_t)cap * sizeof(orc_tap));
+            Ak = (double *)malloc((size_t)cap * sizeof(double));
+            E = (double *)malloc((size_t)cap * 4 * sizeof(double));
+            F = (double *)malloc((size_t)cap * sizeof(double));
+            J = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+            if (!taps || !Ak || !E || !F || !J) { rc = ORC_EINVAL; break; }
+        }
+        double A = 0.0;
+        int64_t n = 0;
+        while (n < ray.n) {
+            double t = (double)ray.t_near + ((double)n + 0.5) * (double)ray.delta;
+            double q[3];
+            for (int a = 0; a < 3; ++a) q[a] = (((double)ray.o[a] + t * (double)ray.d[a]) * (double)M[a]) / Nd[a] - 0.5;
+            dense_tap(vol, M, q, &taps[n]);
+            double raw = taps[n].raw;
+            double v = raw < 0.0 ? 0.0 : (raw > 1.0 ? 1.0 : raw);
+            dense_lookup(lut, nlut, v, &E[n * 4], &J[n], &F[n]);
+            Ak[n] = A;
+            A += (1.0 - A) * E[n * 4 + 3];
+            ++n;
+            if (A >= alpha_stop) break;
+        }
+        const double *g = &g_rgba[lin * 4];
+        double gA = g[3];
+        for (int64_t k = n - 1; k >= 0; --k) {
+            const double *e = &E[k * 4];
+            double w = (1.0 - Ak[k]) * e[3];
+            double gw = g[0] * e[0] + g[1] * e[1] + g[2] * e[2] + gA;
+            double ge[4] = {g[0] * w, g[1] * w, g[2] * w, gw * (1.0 - Ak[k])};
+            gA = gA - gw * e[3];
+            int64_t j = J[k];
+            double f = F[k];
+            double gv = 0.0;
+            for (int ch = 0; ch < 4; ++ch) {
+                g_lut[j * 4 + ch] += (1.0 - f) * ge[ch];
+                g_lut[(j + 1) * 4 + ch] += f * ge[ch];
+                gv += ge[ch] * (lut[(j + 1) * 4 + ch] - lut[j * 4 + ch]);
+            }
+            gv *= (double)(nlut - 1);
+            if (!(taps[k].raw > 0.0 && taps[k].raw < 1.0)) gv = 0.0;
+            for (int c = 0; c < 8; ++c) g_vol[taps[k].idx[c]] += taps[k].w[c] * gv;
+        }
+    }
+    free(taps); free(Ak); free(E); free(F); free(J);
+    return rc;
 }
