@@ -9,7 +9,7 @@ steps.  The input (14.6 GB) is larger than L2, so no flush is needed between
 steps.  Multi-GPU runs are independent replicas (weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mctp|reference]
-                  [--workload full|mid|slab|small|batch|serve]
+                  [--workload full|mid|slab|small|batch|serve|fit]
 
 --workload batch: 64 u8 phantoms with axes ~ U{384..1024} (22 GB resident),
 each through histogram, Otsu and a 256^3 slicemap, then 12 views of each at
@@ -22,6 +22,12 @@ launches on the same slicemaps.
 1024^2, azimuth U[0, 360), elevation U[-60, 60], one of 8 transfer
 functions) at swept rates, served by the continuous-batching server and by
 one render_views launch per request; p50/p99 latency and samples/s per rate.
+
+--workload fit: a 1024^3 u8 phantom rendered from its full-resolution level
+at 24 views 512^2 (azimuth 15k deg, elevation alternating +-20 deg) as FP32
+targets; a 128^3 FP32 reduced volume (started from the 128^3 slicemap level)
+and its 256-entry LUT are fitted by Adam through the adjoint ray march; a
+step is one iteration (forward, loss, adjoint, two Adam updates).
 """
 from __future__ import annotations
 
@@ -62,6 +68,14 @@ def workload(name: str):
                     az_step=10.0, desc="slab (profiling): u16 12-bit 2016x2016x224 phantom (1.8 GB) with the full "
                                        "workload's footprints, 4096 bins, Otsu, levels 512x512x64/256x256x32/"
                                        "128x128x16, 4 views 1024x1024")
+    if name == "fit":
+        spec = phantom.VolumeSpec(1024, 1024, 1024, bits=8, seed=1004, n_ell=12, n_cyl=0)
+        return dict(spec=spec, bits=8, nbins=256, level0=(1024, 1024, 1024), nlevels=4, nviews=24, size=512,
+                    az_step=15.0, elevation=20.0,
+                    desc="fit: u8 1024^3 phantom (1.07 GB), Otsu, slicemap 1024^3..128^3; 24 target views 512x512 "
+                         "(az 15k deg, el +-20 deg) of the 1024^3 level, LUT preset 5; fit 128^3 FP32 volume + "
+                         "256x4 LUT by Adam (lr 1e-2 / 5e-3) through the adjoint march (checkpoints every 64 "
+                         "samples), step 0.5 level voxel, alpha_stop 0.99")
     if name == "serve":
         specs = phantom.serve_specs(200)
         return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=2, nviews=1,
@@ -634,6 +648,141 @@ def run_batch(args, wl):
     return 0
 
 
+def run_fit(args, wl):
+    """The differentiable workload: Adam iterations fitting a 128^3 volume and its LUT."""
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    from paper_2311_15038_gb300 import diff
+    from paper_2311_15038_gb300 import pipeline as pl
+    mctp._lib.load()
+
+    spec = wl["spec"]
+    vol = torch.empty(spec.shape, dtype=torch.uint8, device=dev)
+    phantom.generate_gpu(spec, vol)
+    h, _ = mctp.build_histogram(vol, 8, 256)
+    keep, _ = mctp.select_threshold(h, 256)
+    sm = mctp.Slicemap.allocate((spec.nx, spec.ny, spec.nz), wl["level0"], wl["nlevels"], torch.uint8, 8, dev)
+    mctp.build_slicemap(vol, 8, sm, keep)
+    lut = torch.from_numpy(phantom.preset_luts()[5]).to(dev)
+    n = wl["nviews"]
+    views = [mctp.View(wl["az_step"] * k, wl["elevation"] if k % 2 == 0 else -wl["elevation"], wl["size"],
+                       wl["size"], 0, 0.5) for k in range(n)]
+    targets, _ = mctp.render_views(sm, views, lut, 0.99)
+    # start: the coarsest level (128^3) as intensities
+    k = wl["nlevels"] - 1
+    mx, my, mz = sm.dims[k]
+    tx, ty = sm.tiles[k]
+    start = (sm.atlases[k].view(ty, my, tx, mx).permute(0, 2, 1, 3).reshape(ty * tx, my, mx)[:mz]
+             .float().div_(255.0).contiguous())
+    fviews = [mctp.View(v.azimuth_deg, v.elevation_deg, v.width, v.height, 0, 0.5) for v in views]
+    stream = torch.cuda.Stream(dev)
+    fit = diff.Fitter(start, lut, fviews, (spec.nx, spec.ny, spec.nz), targets, 0.99, 1e-2, 5e-3, stream)
+    torch.cuda.synchronize(dev)
+    loss0 = fit.evaluate()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            fit.step()
+    torch.cuda.synchronize(dev)
+    samples_fwd = int(fit.samples.item())
+    # per-stage times of one iteration
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    s = stream
+    with torch.cuda.stream(s):
+        ev[0].record(s)
+        diff.render_dense(fit.vol, fit.lut, fviews, fit.src_dims, 0.99, fit.images, fit.samples, s)
+        ev[1].record(s)
+        diff.l2_loss(fit.images, fit.targets, fit.scale, fit.g_img, fit.loss, s)
+        ev[2].record(s)
+        diff.render_dense_backward(fit.vol, fit.lut, fviews, fit.src_dims, fit.g_img, 0.99, fit.g_vol, fit.g_lut, s)
+        ev[3].record(s)
+        diff.adam_step(fit.vol, fit.g_vol, fit.m_vol, fit.v_vol, fit.t + 1, 0.0, lo=0.0, hi=1.0, stream=s)
+        diff.adam_step(fit.lut, fit.g_lut, fit.m_lut, fit.v_lut, fit.t + 1, 0.0, lo=0.0, hi=1.0, stream=s)
+        ev[4].record(s)
+    torch.cuda.synchronize(dev)
+    stage_ms = dict(forward=ev[0].elapsed_time(ev[1]), loss=ev[1].elapsed_time(ev[2]),
+                    adjoint=ev[2].elapsed_time(ev[3]), adam=ev[3].elapsed_time(ev[4]))
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    with torch.cuda.stream(s):
+        for _ in range(args.steps):
+            fit.step()
+    t1.record(s)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    # end to end: each iteration's loss read back to pinned host memory
+    loss_host = torch.empty(1, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 10))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    with torch.cuda.stream(s):
+        for _ in range(e2e_steps):
+            fit.step()
+            loss_host.copy_(fit.loss, non_blocking=True)
+    e1.record(s)
+    torch.cuda.synchronize(dev)
+    e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
+    loss1 = fit.evaluate()
+    if ws > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    def psnr(loss):  # loss = mean squared error over RGBA
+        return float(10.0 * np.log10(1.0 / max(loss, 1e-30)))
+
+    if rank != 0:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+        return 0
+    pk = peaks()
+    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    it_s = elapsed / args.steps
+    ach = FP32_FLOPS_PER_SAMPLE * samples_fwd / (stage_ms["forward"] / 1e3) / 1e12
+    line = dict(
+        metric=METRIC, value=samples_fwd * args.steps * ws / elapsed, unit=UNIT, n_gpus=ws, steps=args.steps,
+        warmup=args.warmup, ms_per_step=it_s * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32", data="synthetic",
+        config=dict(workload=wl["desc"], l2="fitted volume 8.4 MB (L2-resident); targets 100 MB",
+                    parallelism=f"replicas x{ws}"),
+        samples_per_step=samples_fwd,
+        stage_ms=stage_ms,
+        forward_samples_per_s=samples_fwd / (stage_ms["forward"] / 1e3),
+        adjoint_samples_per_s=samples_fwd / (stage_ms["adjoint"] / 1e3),
+        loss=dict(start=loss0, end=loss1, iterations=args.warmup + args.steps + e2e_steps, psnr_start_db=psnr(loss0),
+                  psnr_end_db=psnr(loss1)),
+        roofline=dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                      kernel="dense_forward_kernel", traffic=None,
+                      peak_source="FP32 issue rate at the maximum SM clock"),
+        gpu_launches=5 * args.steps,
+        clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
+        e2e=dict(value=samples_fwd / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=4,
+                 ms_per_step=e2e_s * 1e3, note="targets and parameters stay resident; every iteration's loss is "
+                                                "copied to pinned host memory"),
+    )
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_serve(args, wl):
     """The serving workload: rate sweep, batched server against per-view launches."""
     import torch
@@ -748,7 +897,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small", "batch", "serve"])
+    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small", "batch", "serve", "fit"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = workload(args.workload)
@@ -758,6 +907,8 @@ def main():
         return run_batch(args, wl)
     if args.workload == "serve":
         return run_serve(args, wl)
+    if args.workload == "fit":
+        return run_fit(args, wl)
     return run_gpu(args, wl)
 
 

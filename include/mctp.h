@@ -362,6 +362,52 @@ int mctp_server_destroy(mctp_server *server);
 /* Monotonic host clock, seconds. */
 double mctp_now(void);
 
+/*
+ * Differentiable rendering of a reduced volume (the previews stand a reduced
+ * volume in for the full one, Sec. I / Sec. III; fitting it so that its
+ * renders match renders of the source is an extension of this library).
+ *   vol       device float [mz][my][mx] intensities; the value at a sample is
+ *             v = min(max(trilinear(vol), 0), 1), looked up in lut_rgba as in
+ *             mctp_render_views (x = v (nlut - 1), linear between entries)
+ *   src_dims  host int64[3]: the world box [0,nx]x[0,ny]x[0,nz] the volume
+ *             spans (views and sample spacing as in mctp_render_views, with
+ *             the volume as the only level: every view's level must be 0)
+ *   out_rgba  device float, 16-byte aligned, images one after another
+ *   samples_taken device uint64[1] or NULL: overwritten with the samples
+ *             marched (up to and including each ray's early-exit sample)
+ * No empty-space skipping (the transfer function is a variable here).
+ * Errors: MCTP_EINVAL, MCTP_ESIZE (more than 2^31 voxels), MCTP_ECUDA.
+ */
+int mctp_render_dense(const float *vol, int32_t mx, int32_t my, int32_t mz, const int64_t *src_dims,
+                      const mctp_view *views, int32_t nviews, const float *lut_rgba, int32_t nlut,
+                      float alpha_stop, float *out_rgba, uint64_t *samples_taken, void *stream);
+
+/*
+ * Gradient of L with respect to vol and lut_rgba, given grad_rgba = dL/d(the
+ * images of mctp_render_dense with the same arguments).  grad_vol (float,
+ * like vol) and grad_lut (float [nlut][4]) are overwritten.  The stop index
+ * of each ray's early exit is held fixed; where the intensity clamp is active
+ * the volume gradient is 0.  The adjoint walks each ray back to front with
+ * checkpoints every 64 samples (rays of up to 2048 samples: MCTP_ESIZE for
+ * views whose sample spacing allows longer rays).  Results are accumulated
+ * with float atomics, so the last bits vary between runs.
+ */
+int mctp_render_dense_backward(const float *vol, int32_t mx, int32_t my, int32_t mz, const int64_t *src_dims,
+                               const mctp_view *views, int32_t nviews, const float *lut_rgba, int32_t nlut,
+                               float alpha_stop, const float *grad_rgba, float *grad_vol, float *grad_lut,
+                               void *stream);
+
+/* loss (device float[1], overwritten) = scale * sum_i (x_i - target_i)^2;
+ * grad (device, may be NULL) = 2 scale (x - target). */
+int mctp_l2_loss(const float *x, const float *target, int64_t n, float scale, float *grad, float *loss,
+                 void *stream);
+
+/* One Adam step (Kingma & Ba) on n parameters with bias correction for step
+ * number `step` (>= 1), then clamped to [lo, hi]; m and v are the moment
+ * buffers (start them at zero). */
+int mctp_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
+                   float beta2, float eps, int32_t step, float lo, float hi, void *stream);
+
 /* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
  * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
 int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);

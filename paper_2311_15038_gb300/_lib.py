@@ -94,6 +94,13 @@ EXPORTS = {
                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "mctp_server_destroy": ([C_VP], ctypes.c_int),
     "mctp_now": ([], ctypes.c_double),
+    "mctp_render_dense": ([C_VP, C_I32, C_I32, C_I32, C_VP, ctypes.POINTER(ViewDesc), C_I32, C_VP, C_I32,
+                           ctypes.c_float, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_render_dense_backward": ([C_VP, C_I32, C_I32, C_I32, C_VP, ctypes.POINTER(ViewDesc), C_I32, C_VP, C_I32,
+                                    ctypes.c_float, C_VP, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_l2_loss": ([C_VP, C_VP, C_I64, ctypes.c_float, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_adam_step": ([C_VP, C_VP, C_VP, C_VP, C_I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                        ctypes.c_float, C_I32, ctypes.c_float, ctypes.c_float, C_VP], ctypes.c_int),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),

@@ -296,6 +296,31 @@ def test_server_rejects(lib):
     assert lib.mctp_now() > 0.0
 
 
+def test_dense_rejects(lib):
+    from paper_2311_15038_gb300 import _lib
+    src = (ctypes.c_int64 * 3)(64, 64, 64)
+    v = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 16, 16, 0, 0.5))
+    v1 = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 16, 16, 1, 0.5))      # only level 0 exists
+    fine = (_lib.ViewDesc * 1)(_lib.ViewDesc(0.0, 0.0, 16, 16, 0, 1.0 / 256))  # rays of > 2048 samples
+
+    def fwd(vol=FAKE, m=(16, 16, 16), views=v, lut=FAKE, nlut=16, stop=0.99, out=FAKE, srcd=src):
+        return lib.mctp_render_dense(vol, *m, srcd, views, 1, lut, nlut, stop, out, None, None)
+    assert fwd(vol=None) == -1
+    assert fwd(m=(0, 16, 16)) == -1
+    assert fwd(views=v1) == -1
+    assert fwd(nlut=1) == -1
+    assert fwd(stop=1.5) == -1
+    assert fwd(out=ctypes.c_void_p(0x10004)) == -1
+    assert fwd(srcd=None) == -1
+    assert fwd(m=(2048, 2048, 1024)) == -3
+    assert lib.mctp_render_dense_backward(FAKE, 16, 16, 16, src, fine, 1, FAKE, 16, 0.99, FAKE, FAKE, FAKE,
+                                          None) == -3  # refused on the host before anything is enqueued
+    assert lib.mctp_render_dense_backward(FAKE, 16, 16, 16, src, v, 1, FAKE, 16, 0.99, None, FAKE, FAKE, None) == -1
+    assert lib.mctp_l2_loss(None, FAKE, 4, 1.0, None, FAKE, None) == -1
+    assert lib.mctp_adam_step(FAKE, FAKE, FAKE, FAKE, 4, 0.1, 0.9, 0.999, 1e-8, 0, 0.0, 1.0, None) == -1
+    assert lib.mctp_adam_step(FAKE, FAKE, FAKE, FAKE, 4, 0.1, 1.0, 0.999, 1e-8, 1, 0.0, 1.0, None) == -1
+
+
 def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
     from paper_2311_15038_gb300 import _lib, build
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
