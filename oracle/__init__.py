@@ -59,13 +59,15 @@ def _L():
                                                      C_VP, C_VP, C_VP, C_VP, C_VP]
         lib.orc_entropy.argtypes = [C_VP, ctypes.c_int, C_VP]
         lib.orc_maxgrid.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, ctypes.c_int, C_VP]
+        lib.orc_image_histogram.argtypes = [C_VP, C_I64, C_VP]
         lib.orc_render_dense.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
                                                                ctypes.POINTER(View), C_VP, C_I64, C_VP, C_VP]
         lib.orc_render_dense_grad.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
                                                                     ctypes.POINTER(View), C_VP, C_VP, C_VP]
         for f in ("orc_histogram", "orc_otsu", "orc_its", "orc_keep_threshold", "orc_keep_topslab",
                   "orc_filter", "orc_downsample", "orc_atlas_pack", "orc_render", "orc_ray_params",
-                  "orc_entropy", "orc_maxgrid", "orc_render_dense", "orc_render_dense_grad"):
+                  "orc_entropy", "orc_maxgrid", "orc_render_dense", "orc_render_dense_grad",
+                  "orc_image_histogram"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -277,3 +279,16 @@ def render_dense_grad(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el:
     _check(_L().orc_render_dense_grad(_p(vol), mx, my, mz, nx, ny, nz, _p(lut), lut.shape[0], alpha_stop,
                                       ctypes.byref(v), _p(g), _p(gv), _p(gl)), "render_dense_grad")
     return gv, gl
+
+
+def image_histogram(rgba: np.ndarray) -> np.ndarray:
+    """256-bin grey-level histogram of a float32 RGBA image (any leading shape)."""
+    a = np.ascontiguousarray(rgba, dtype=np.float32).reshape(-1, 4)
+    h = np.zeros(256, np.uint64)
+    _check(_L().orc_image_histogram(_p(a), a.shape[0], _p(h)), "image_histogram")
+    return h
+
+
+def image_entropy(rgba: np.ndarray) -> float:
+    """Eq. 2 over the image's grey-level histogram."""
+    return entropy(image_histogram(rgba))

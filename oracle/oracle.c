@@ -28,6 +28,8 @@
  *   orc_render      Beer-Lambert slab closed form, axis-aligned views against a
  *                   product-form compositor over scipy map_coordinates samples,
  *                   empty volume, axis-aligned sample counts
+ *   orc_image_histogram   grey pixels land in round(v*255), primaries at their
+ *                         luminance weights, counts sum to the pixel count
  *   orc_render_dense      orc_render on the same level (intensities = raw/255),
  *                         Beer-Lambert slab
  *   orc_render_dense_grad central finite differences of orc_render_dense along
@@ -822,4 +824,26 @@ int orc_render_dense_grad(const double *vol, int64_t mx, int64_t my, int64_t mz,
     }
     free(taps); free(Ak); free(E); free(F); free(J);
     return rc;
+}
+
+/*
+ * 256-bin grey-level histogram of a rendered image, the p_i of Eq. 2
+ * (Sec. III-C).  Reading: the image is the premultiplied RGBA render shown
+ * over a black background; its grey level is the Rec. 709 luminance
+ * lum = (0.2126 R + 0.7152 G) + 0.0722 B, computed in FP32 in this order
+ * (one rounding per operation), clamped to [0, 1] and quantised to 8 bits
+ * as floor(lum * 255 + 0.5).
+ */
+int orc_image_histogram(const float *rgba, int64_t npix, uint64_t *hist)
+{
+    if ((!rgba && npix) || !hist || npix < 0) return ORC_EINVAL;
+    for (int i = 0; i < 256; ++i) hist[i] = 0;
+    for (int64_t p = 0; p < npix; ++p) {
+        float lum = (0.2126f * rgba[p * 4 + 0] + 0.7152f * rgba[p * 4 + 1]) + 0.0722f * rgba[p * 4 + 2];
+        lum = lum < 0.0f ? 0.0f : (lum > 1.0f ? 1.0f : lum);
+        if (!(lum == lum)) lum = 0.0f; /* NaN counts as black */
+        int q = (int)floorf(lum * 255.0f + 0.5f);
+        hist[q] += 1;
+    }
+    return ORC_OK;
 }

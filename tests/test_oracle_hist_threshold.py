@@ -242,3 +242,17 @@ def test_entropy_closed_forms(orc):
     assert orc.entropy(np.array([5, 5, 0, 0], np.uint64)) == pytest.approx(1.0, abs=1e-15)
     p = np.array([1, 2, 3, 4], np.float64) / 10
     assert orc.entropy(np.array([1, 2, 3, 4], np.uint64)) == pytest.approx(-(p * np.log2(p)).sum(), rel=1e-14)
+
+
+def test_image_histogram_pins(orc):
+    # grey pixels (R = G = B = k/255) have luminance k/255: bin k
+    k = np.arange(256, dtype=np.float32) / np.float32(255.0)
+    grey = np.stack([k, k, k, np.ones(256, np.float32)], axis=1)
+    assert np.array_equal(orc.image_histogram(grey), np.ones(256, np.uint64))
+    assert orc.image_entropy(grey) == pytest.approx(8.0, abs=1e-12)
+    # primaries land at their luminance weights: round(0.2126*255)=54, round(0.7152*255)=182, round(0.0722*255)=18
+    prim = np.array([[1, 0, 0, 1], [0, 1, 0, 1], [0, 0, 1, 1], [0, 0, 0, 0], [2.0, 2.0, 2.0, 1.0]], np.float32)
+    h = orc.image_histogram(prim)
+    assert h[54] == 1 and h[182] == 1 and h[18] == 1 and h[0] == 1 and h[255] == 1 and h.sum() == 5
+    # a black image carries no information
+    assert orc.image_entropy(np.zeros((7, 9, 4), np.float32)) == 0.0
