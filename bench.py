@@ -95,26 +95,32 @@ def workload(name: str):
                 az_step=0.0, desc="small: u8 256^3 phantom, 256 bins, Otsu, level 128^3, 1 view 256x256")
 
 
-KERNEL_SOURCES = {"histogram": "hist.cu", "slicemap": "slicemap.cu", "render": "render.cu",
-                  "threshold": "threshold.cu"}
+KERNEL_SOURCES = {"histogram": ["hist.cu"], "slicemap": ["slicemap.cu", "slicemap_common.cuh"],
+                  "render": ["render.cu", "render_common.cuh"], "threshold": ["threshold.cu"]}
+
+
+def source_sha256(files) -> str:
+    """SHA-256 over the kernel's source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2311_15038_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def measured_traffic():
     """ncu DRAM bytes per launch (profiles/traffic.json), kept only while the
-    kernel's source file is unchanged since the counters were taken."""
-    import hashlib
+    kernel's source files are unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     out = {}
     if not os.path.exists(path):
         return out
     rec = json.load(open(path))
-    for kernel, src in KERNEL_SOURCES.items():
+    for kernel, files in KERNEL_SOURCES.items():
         r = rec.get(kernel)
         if not r:
             continue
-        f = os.path.join(ROOT, "paper_2311_15038_gb300", "csrc", src)
-        sha = hashlib.sha256(open(f, "rb").read()).hexdigest()
-        out[kernel] = r["bytes_per_launch"] if sha == r.get("source_sha256") else None
+        out[kernel] = r["bytes_per_launch"] if source_sha256(files) == r.get("source_sha256") else None
     return out
 
 
@@ -174,9 +180,9 @@ def launches_per_step(wl, nviews):
     """Kernels of this library launched by one step: histogram, threshold
     selection, the level-0 slicemap kernel (levels 1-2 fused), one 2x2x2 kernel
     per further level, one max-grid kernel per level, one render launch per 64
-    views."""
+    views, one image-histogram launch per 1024 views and the entropy kernel."""
     nl = wl["nlevels"]
-    return 1 + 1 + 1 + max(0, nl - 3) + nl + (nviews + 63) // 64
+    return 1 + 1 + 1 + max(0, nl - 3) + nl + (nviews + 63) // 64 + (nviews + 1023) // 1024 + 1
 
 
 def dist_setup():
@@ -300,7 +306,7 @@ def run_gpu(args, wl):
     stream = torch.cuda.Stream(dev)
     pipe = pl.PreviewPipeline(cfg, dtype, dev, stream)
 
-    stages = ["histogram", "threshold", "slicemap", "render"]
+    stages = ["histogram", "threshold", "slicemap", "render", "entropy"]
     ev = {}
 
     def timer(name):
@@ -384,6 +390,7 @@ def run_gpu(args, wl):
         "slicemap": dict(bound="hbm", bytes=vol_bytes + atlas_bytes, unit="GB/s"),
         "render": dict(bound="alu", flops=FP32_FLOPS_PER_SAMPLE * samples_per_step, unit="TFLOP/s"),
         "threshold": dict(bound="alu", flops=0, unit="TFLOP/s"),
+        "entropy": dict(bound="hbm", bytes=image_bytes, unit="GB/s"),
     }
     fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     traffic = measured_traffic() if args.workload == "full" else {}
@@ -402,10 +409,13 @@ def run_gpu(args, wl):
     dominant = max(stage_ms, key=stage_ms.get)
     steps_total = samples_per_step * args.steps * ws
     value = steps_total / elapsed
+    best_view = int(pipe.best.item())
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
         ms_per_step=elapsed * 1e3 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="u16/f32", data="synthetic",
+        best_view=dict(index=best_view, azimuth_deg=views[best_view].azimuth_deg,
+                       entropy_bits=float(pipe.entropy[best_view].item())),
         config=dict(workload=wl["desc"], l2="inputs larger than L2 (14.6 GB volume; no flush)"
                     if vol_bytes > 200e6 else "input fits in L2 (L2-resident numbers)",
                     parallelism=f"replicas x{ws}"),

@@ -408,6 +408,25 @@ int mctp_l2_loss(const float *x, const float *target, int64_t n, float scale, fl
 int mctp_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
                    float beta2, float eps, int32_t step, float lo, float hi, void *stream);
 
+/*
+ * Information content of rendered views, for choosing the most informative
+ * snapshot (Sec. III-C, Eq. 2): per view the Shannon entropy
+ * H = -sum_i p_i log2 p_i of its 256-bin grey-level histogram, and the view
+ * with the largest H.  Grey level of a pixel (the premultiplied render over
+ * black): Rec. 709 luminance (0.2126 R + 0.7152 G) + 0.0722 B in FP32 with one
+ * rounding per operation in this order, clamped to [0, 1] (NaN as 0),
+ * quantised as floor(lum * 255 + 0.5).
+ *   rgba     device float, 16-byte aligned, views one after another (the
+ *            layout of mctp_render_views' output)
+ *   views    host array (only width and height are used), nviews <= 65535
+ *   hist     device uint64[nviews][256], overwritten
+ *   entropy  device double[nviews], overwritten (bits)
+ *   best     device int32[1] or NULL: index of the largest H (lowest index
+ *            on ties; -1 for no views)
+ */
+int mctp_image_entropy(const float *rgba, const mctp_view *views, int32_t nviews, uint64_t *hist,
+                       double *entropy, int32_t *best, void *stream);
+
 /* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
  * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
 int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import MctpError  # noqa: F401
 
 __all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
-           "render_batch", "render_batch_workspace", "render_batch_static", "BatchTuning", "Slicemap", "View", "default_tiles",
+           "render_batch", "render_batch_workspace", "render_batch_static", "BatchTuning", "image_entropy", "Slicemap", "View", "default_tiles",
            "atlas_bytes", "version", "MctpError"]
 
 _DTYPES = {torch.uint8: (_lib.MCTP_U8, 1), torch.uint16: (_lib.MCTP_U16, 2), torch.int16: (_lib.MCTP_U16, 2)}
@@ -319,3 +319,20 @@ def render_batch_static(slicemaps, views, view_slicemap, view_lut, luts: torch.T
                                                     _ptr(out), _ptr(samples), _stream(stream)),
                "mctp_render_batch_static")
     return out, samples
+
+
+def image_entropy(flat: torch.Tensor, views, hist: torch.Tensor | None = None, entropy: torch.Tensor | None = None,
+                  best: torch.Tensor | None = None, stream=None):
+    """Eq. 2 per view of a render_views buffer -> (hist uint64[V][256], H float64[V], best int32[1])."""
+    _cuda(flat, "images")
+    dev = flat.device
+    n = len(views)
+    if hist is None:
+        hist = torch.empty((max(n, 1), 256), dtype=torch.uint64, device=dev)
+    if entropy is None:
+        entropy = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    if best is None:
+        best = torch.empty(1, dtype=torch.int32, device=dev)
+    _lib.check(_lib.load().mctp_image_entropy(_ptr(flat), view_array(views), n, _ptr(hist), _ptr(entropy), _ptr(best),
+                                              _stream(stream)), "mctp_image_entropy")
+    return hist, entropy, best

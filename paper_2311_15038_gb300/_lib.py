@@ -101,6 +101,7 @@ EXPORTS = {
     "mctp_l2_loss": ([C_VP, C_VP, C_I64, ctypes.c_float, C_VP, C_VP, C_VP], ctypes.c_int),
     "mctp_adam_step": ([C_VP, C_VP, C_VP, C_VP, C_I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                         ctypes.c_float, C_I32, ctypes.c_float, ctypes.c_float, C_VP], ctypes.c_int),
+    "mctp_image_entropy": ([C_VP, ctypes.POINTER(ViewDesc), C_I32, C_VP, C_VP, C_VP, C_VP], ctypes.c_int),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),

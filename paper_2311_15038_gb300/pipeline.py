@@ -1,14 +1,15 @@
 """The preview hot path as one reusable object: histogram -> threshold keep
-table -> fused filter + slicemap -> rendered views, all enqueued on one CUDA
-stream with outputs allocated once (arXiv 2311.15038, Table I pipelines:
-thresholding, slicemap conversion, server-side rendering)."""
+table -> fused filter + slicemap -> rendered views -> the most informative
+view (Eq. 2), all enqueued on one CUDA stream with outputs allocated once
+(arXiv 2311.15038, Table I pipelines: thresholding, slicemap conversion,
+server-side rendering with the optimal image snapshot)."""
 from __future__ import annotations
 
 from dataclasses import dataclass
 
 import torch
 
-from . import Slicemap, View, build_histogram, build_slicemap, render_views, select_threshold
+from . import Slicemap, View, build_histogram, build_slicemap, image_entropy, render_views, select_threshold
 
 
 @dataclass
@@ -46,6 +47,10 @@ class PreviewPipeline:
         total = sum(v.width * v.height * 4 for v in cfg.views)
         self.images = torch.empty(max(total, 4), dtype=torch.float32, device=self.device)
         self.samples = torch.empty(1, dtype=torch.uint64, device=self.device)
+        nv = max(len(cfg.views), 1)
+        self.image_hist = torch.empty((nv, 256), dtype=torch.uint64, device=self.device)
+        self.entropy = torch.empty(nv, dtype=torch.float64, device=self.device)
+        self.best = torch.empty(1, dtype=torch.int32, device=self.device)
 
     def run(self, vol: torch.Tensor, lut: torch.Tensor, timer=None):
         """Enqueue one pass; `timer(name)` (optional) is called between the steps."""
@@ -66,5 +71,7 @@ class PreviewPipeline:
         build_slicemap(vol, c.bits, self.sm, keep, self.stream)
         mark("render")
         render_views(self.sm, c.views, lut, c.alpha_stop, self.images, self.samples, self.stream)
+        mark("entropy")
+        image_entropy(self.images, c.views, self.image_hist, self.entropy, self.best, self.stream)
         mark("end")
         return self.images, self.samples
