@@ -60,6 +60,9 @@ def _L():
         lib.orc_entropy.argtypes = [C_VP, ctypes.c_int, C_VP]
         lib.orc_maxgrid.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, ctypes.c_int, C_VP]
         lib.orc_image_histogram.argtypes = [C_VP, C_I64, C_VP]
+        lib.orc_hough_circle.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, C_VP, C_VP, C_VP, C_VP, C_VP, C_VP]
+        lib.orc_mask_circle.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, C_I32, C_I32, C_I32, C_VP]
         lib.orc_render_dense.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
                                                                ctypes.POINTER(View), C_VP, C_I64, C_VP, C_VP]
         lib.orc_render_dense_grad.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
@@ -67,7 +70,7 @@ def _L():
         for f in ("orc_histogram", "orc_otsu", "orc_its", "orc_keep_threshold", "orc_keep_topslab",
                   "orc_filter", "orc_downsample", "orc_atlas_pack", "orc_render", "orc_ray_params",
                   "orc_entropy", "orc_maxgrid", "orc_render_dense", "orc_render_dense_grad",
-                  "orc_image_histogram"):
+                  "orc_image_histogram", "orc_hough_circle", "orc_mask_circle"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -292,3 +295,25 @@ def image_histogram(rgba: np.ndarray) -> np.ndarray:
 def image_entropy(rgba: np.ndarray) -> float:
     """Eq. 2 over the image's grey-level histogram."""
     return entropy(image_histogram(rgba))
+
+
+def hough_circle(slice2d: np.ndarray, thr: int, rmin: int, rmax: int, cell: int):
+    """Container circle of a slice [y][x] -> dict(cx, cy, r, fit (cx, cy, r floats), acc, rhist)."""
+    sl = _vol(slice2d[None])[0]
+    ny, nx = sl.shape
+    acc = np.zeros((-(-ny // cell), -(-nx // cell)), np.uint32)
+    rh = np.zeros(rmax + 1, np.uint32)
+    fit = np.zeros(3, np.float64)
+    out = np.zeros(3, np.int32)
+    _check(_L().orc_hough_circle(_p(sl), sl.itemsize, nx, ny, thr, rmin, rmax, cell, _p(acc), _p(rh), _p(fit),
+                                 _p(out[0:1]), _p(out[1:2]), _p(out[2:3])), "hough_circle")
+    return dict(cx=int(out[0]), cy=int(out[1]), r=int(out[2]), fit=fit, acc=acc, rhist=rh)
+
+
+def mask_circle(vol: np.ndarray, cx: int, cy: int, r_keep: int) -> np.ndarray:
+    """vol [z][y][x] with every voxel outside the circle set to 0."""
+    vol = _vol(vol)
+    nz, ny, nx = vol.shape
+    out = np.empty_like(vol)
+    _check(_L().orc_mask_circle(_p(vol), vol.itemsize, nx, ny, nz, cx, cy, r_keep, _p(out)), "mask_circle")
+    return out

@@ -28,6 +28,10 @@
  *   orc_render      Beer-Lambert slab closed form, axis-aligned views against a
  *                   product-form compositor over scipy map_coordinates samples,
  *                   empty volume, axis-aligned sample counts
+ *   orc_hough_circle      drawn rings of known centre and radius, the phantom
+ *                         container's axis and inner radius, an image without
+ *                         edges
+ *   orc_mask_circle       hand-counted disks, identity for a covering circle
  *   orc_image_histogram   grey pixels land in round(v*255), primaries at their
  *                         luminance weights, counts sum to the pixel count
  *   orc_render_dense      orc_render on the same level (intensities = raw/255),
@@ -845,5 +849,185 @@ int orc_image_histogram(const float *rgba, int64_t npix, uint64_t *hist)
         int q = (int)floorf(lum * 255.0f + 0.5f);
         hist[q] += 1;
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------ container removal */
+
+/*
+ * Container circle of one slice (Sec. III, Container Removal: a Hough circle
+ * transform on the top slice; everything outside the circle is then dropped
+ * from every slice).  The cited transform (Ioannou, Huda and Laine 1999) finds
+ * the centre by a 2D vote along each edge pixel's gradient line and the radius
+ * from a histogram of edge distances; the paper gives no further detail.
+ * Reading, step by step (integers unless stated):
+ *  1. Smooth: b = separable [1 4 6 4 1] x [1 4 6 4 1] filter of the slice,
+ *     indices clamped at the borders (b is 256 x the grey scale).
+ *  2. Sobel gradient of b at interior pixels 1..nx-2, 1..ny-2:
+ *     gx = (b[y-1][x+1] + 2 b[y][x+1] + b[y+1][x+1]) - (same at x-1), gy likewise.
+ *  3. Edge pixel: gx^2 + gy^2 >= (256 thr)^2.
+ *  4. Unit gradient in FP32, one rounding per operation:
+ *     m = sqrt((float)(gx^2 + gy^2)), ux = (float)gx / m, uy = (float)gy / m.
+ *  5. Coarse centre: for t = rmin..rmax the point (x - t ux, y - t uy) (FP32)
+ *     votes for its cell (floor(fx / s), floor(fy / s)) of a grid of s x s
+ *     pixel cells (votes against the gradient: the circle whose inside is
+ *     darker than its rim, the container's inner wall around the air inside);
+ *     the cell with most votes (lowest row, then column, on ties) gives the
+ *     centre (cx, cy) = (cell * s + (s - 1) / 2) in FP64.
+ *  6. Coarse radius: over edge pixels whose gradient points away from the
+ *     centre ((x - cx) ux + (y - cy) uy > 0, FP64), r = floor(d + 1/2),
+ *     d = sqrt((x - cx)^2 + (y - cy)^2) (FP64), counted for rmin <= r <= rmax;
+ *     the most frequent r (smallest on ties).
+ *  7. Refinement (an addition: the Hough cells are s pixels wide): three
+ *     least-squares circle fits (Kasa) over the outward edge pixels with
+ *     |d - r| <= w, w = 2s + 3, s + 3, 3: minimise sum (x^2 + y^2 + D x + E y
+ *     + F)^2 from exact integer moment sums, solved by Cramer's rule in FP64;
+ *     centre (-D/2, -E/2), radius sqrt(cx^2 + cy^2 - F).  A fit with fewer
+ *     than 3 pixels or a zero determinant keeps the previous circle.
+ *  8. Result: centre (floor(cx + 1/2), floor(cy + 1/2)), radius floor(r); when
+ *     no outward edge pixel falls in [rmin, rmax] there is no circle: (0, 0, -1).
+ * acc (ceil(ny/s) * ceil(nx/s)) and rhist (rmax + 1) receive the vote counts,
+ * fit (3 doubles) the refined circle, when not NULL.
+ */
+typedef struct {
+    int64_t x, y;
+    float ux, uy;
+} orc_edge;
+
+static int64_t clamp64(int64_t v, int64_t hi) { return v < 0 ? 0 : (v > hi ? hi : v); }
+
+int orc_hough_circle(const void *slice, int esize, int64_t nx, int64_t ny, int64_t thr, int rmin, int rmax, int s,
+                     uint32_t *acc, uint32_t *rhist, double *fit, int32_t *cx_out, int32_t *cy_out, int32_t *r_out)
+{
+    if (!slice || (esize != 1 && esize != 2) || nx < 3 || ny < 3 || thr < 1 || rmin < 0 || rmax < rmin || s < 1 ||
+        !cx_out || !cy_out || !r_out)
+        return ORC_EINVAL;
+    const int64_t k5[5] = {1, 4, 6, 4, 1};
+    int64_t *tmp = (int64_t *)malloc((size_t)(nx * ny) * sizeof(int64_t));
+    int64_t *b = (int64_t *)malloc((size_t)(nx * ny) * sizeof(int64_t));
+    orc_edge *E = (orc_edge *)malloc((size_t)(nx * ny) * sizeof(orc_edge));
+    const int64_t gxn = (nx + s - 1) / s, gyn = (ny + s - 1) / s;
+    uint32_t *A = acc ? acc : (uint32_t *)malloc((size_t)(gxn * gyn) * sizeof(uint32_t));
+    uint32_t *R = rhist ? rhist : (uint32_t *)malloc(((size_t)rmax + 1) * sizeof(uint32_t));
+    if (!tmp || !b || !E || !A || !R) {
+        free(tmp); free(b); free(E);
+        if (!acc) free(A);
+        if (!rhist) free(R);
+        return ORC_EINVAL;
+    }
+    memset(A, 0, (size_t)(gxn * gyn) * sizeof(uint32_t));
+    memset(R, 0, ((size_t)rmax + 1) * sizeof(uint32_t));
+    /* 1. smoothing, x then y */
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t v = 0;
+            for (int i = 0; i < 5; ++i) v += k5[i] * (int64_t)load_voxel(slice, esize, y * nx + clamp64(x + i - 2, nx - 1));
+            tmp[y * nx + x] = v;
+        }
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t v = 0;
+            for (int i = 0; i < 5; ++i) v += k5[i] * tmp[clamp64(y + i - 2, ny - 1) * nx + x];
+            b[y * nx + x] = v;
+        }
+    /* 2-4. edges and their unit gradients */
+    const int64_t t2 = (256 * thr) * (256 * thr);
+    int64_t ne = 0;
+    for (int64_t y = 1; y < ny - 1; ++y)
+        for (int64_t x = 1; x < nx - 1; ++x) {
+#define B(xx, yy) b[(yy) * nx + (xx)]
+            int64_t gx = (B(x + 1, y - 1) + 2 * B(x + 1, y) + B(x + 1, y + 1)) - (B(x - 1, y - 1) + 2 * B(x - 1, y) + B(x - 1, y + 1));
+            int64_t gy = (B(x - 1, y + 1) + 2 * B(x, y + 1) + B(x + 1, y + 1)) - (B(x - 1, y - 1) + 2 * B(x, y - 1) + B(x + 1, y - 1));
+#undef B
+            int64_t g2 = gx * gx + gy * gy;
+            if (g2 < t2) continue;
+            float m = sqrtf((float)g2);
+            E[ne].x = x;
+            E[ne].y = y;
+            E[ne].ux = (float)gx / m;
+            E[ne].uy = (float)gy / m;
+            ++ne;
+        }
+    /* 5. coarse centre */
+    for (int64_t e = 0; e < ne; ++e)
+        for (int t = rmin; t <= rmax; ++t) {
+            float fx = (float)E[e].x - (float)t * E[e].ux, fy = (float)E[e].y - (float)t * E[e].uy;
+            if (!(fx >= 0.0f && fy >= 0.0f)) continue;
+            int64_t ix = (int64_t)floorf(fx / (float)s), iy = (int64_t)floorf(fy / (float)s);
+            if (ix < gxn && iy < gyn) A[iy * gxn + ix] += 1;
+        }
+    int64_t best = 0;
+    for (int64_t i = 1; i < gxn * gyn; ++i)
+        if (A[i] > A[best]) best = i;
+    double cx = (double)((best % gxn) * s) + (double)(s - 1) / 2.0;
+    double cy = (double)((best / gxn) * s) + (double)(s - 1) / 2.0;
+    /* 6. coarse radius */
+    for (int64_t e = 0; e < ne; ++e) {
+        double dx = (double)E[e].x - cx, dy = (double)E[e].y - cy;
+        if (!(dx * (double)E[e].ux + dy * (double)E[e].uy > 0.0)) continue;
+        int64_t r = (int64_t)floor(sqrt(dx * dx + dy * dy) + 0.5);
+        if (r >= rmin && r <= rmax) R[r] += 1;
+    }
+    int rbest = rmin;
+    for (int r = rmin + 1; r <= rmax; ++r)
+        if (R[r] > R[rbest]) rbest = r;
+    double rf = (double)rbest;
+    /* 7. refinement */
+    const double bands[3] = {2.0 * s + 3.0, (double)s + 3.0, 3.0};
+    for (int it = 0; it < 3 && ne > 0 && R[rbest] > 0; ++it) {
+        int64_t n = 0, sxx = 0, sxy = 0, sx = 0, syy = 0, sy = 0, sz = 0, sxz = 0, syz = 0;
+        for (int64_t e = 0; e < ne; ++e) {
+            double dx = (double)E[e].x - cx, dy = (double)E[e].y - cy;
+            if (!(dx * (double)E[e].ux + dy * (double)E[e].uy > 0.0)) continue;
+            if (!(fabs(sqrt(dx * dx + dy * dy) - rf) <= bands[it])) continue;
+            int64_t x = E[e].x, y = E[e].y, z = x * x + y * y;
+            ++n; sxx += x * x; sxy += x * y; sx += x; syy += y * y; sy += y; sz += z; sxz += x * z; syz += y * z;
+        }
+        if (n < 3) break;
+        double a11 = (double)sxx, a12 = (double)sxy, a13 = (double)sx, a22 = (double)syy, a23 = (double)sy;
+        double a33 = (double)n, b1 = -(double)sxz, b2 = -(double)syz, b3 = -(double)sz;
+        double det = a11 * (a22 * a33 - a23 * a23) - a12 * (a12 * a33 - a23 * a13) + a13 * (a12 * a23 - a22 * a13);
+        if (det == 0.0) break;
+        double dD = b1 * (a22 * a33 - a23 * a23) - a12 * (b2 * a33 - a23 * b3) + a13 * (b2 * a23 - a22 * b3);
+        double dE = a11 * (b2 * a33 - b3 * a23) - b1 * (a12 * a33 - a23 * a13) + a13 * (a12 * b3 - b2 * a13);
+        double dF = a11 * (a22 * b3 - a23 * b2) - a12 * (a12 * b3 - b2 * a13) + b1 * (a12 * a23 - a22 * a13);
+        double D = dD / det, Ee = dE / det, F = dF / det;
+        double ncx = -D / 2.0, ncy = -Ee / 2.0, rr2 = ncx * ncx + ncy * ncy - F;
+        if (!(rr2 > 0.0)) break;
+        cx = ncx;
+        cy = ncy;
+        rf = sqrt(rr2);
+    }
+    if (ne == 0 || R[rbest] == 0) {
+        cx = 0.0;
+        cy = 0.0;
+        rf = -1.0;
+    }
+    *cx_out = (int32_t)floor(cx + 0.5);
+    *cy_out = (int32_t)floor(cy + 0.5);
+    *r_out = (int32_t)floor(rf);
+    if (fit) { fit[0] = cx; fit[1] = cy; fit[2] = rf; }
+    free(tmp); free(b); free(E);
+    if (!acc) free(A);
+    if (!rhist) free(R);
+    return ORC_OK;
+}
+
+/* Drop everything outside the container (Sec. III, Container Removal): voxel
+ * (x, y, z) keeps its value when (x - cx)^2 + (y - cy)^2 <= r_keep^2, else 0
+ * (the keep/discard sense of Sec. III-A: "removed" means zero).  r_keep < 0
+ * means no container was found: everything is kept. */
+int orc_mask_circle(const void *in, int esize, int64_t nx, int64_t ny, int64_t nz, int32_t cx, int32_t cy,
+                    int32_t r_keep, void *out)
+{
+    if (!in || !out || (esize != 1 && esize != 2) || nx < 1 || ny < 1 || nz < 1) return ORC_EINVAL;
+    const int64_t rk2 = (int64_t)r_keep * r_keep;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t i = (z * ny + y) * nx + x;
+                int64_t d2 = (x - cx) * (x - cx) + (y - cy) * (y - cy);
+                store_voxel(out, esize, i, (r_keep < 0 || d2 <= rk2) ? load_voxel(in, esize, i) : 0u);
+            }
     return ORC_OK;
 }

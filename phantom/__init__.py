@@ -53,11 +53,13 @@ def _cpu():
         lib = ctypes.CDLL(_CPU_SO)
         lib.ph_make_params.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_int32, ctypes.c_int32,
                                                               ctypes.c_uint64, ctypes.c_int32,
-                                                              ctypes.c_int32, ctypes.c_void_p]
+                                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
         lib.ph_make_params.restype = ctypes.c_int
         lib.ph_generate_cpu.argtypes = [ctypes.c_void_p] + [ctypes.c_int64] * 6 + [ctypes.c_void_p]
         lib.ph_generate_cpu.restype = ctypes.c_int
         lib.ph_params_size.restype = ctypes.c_int
+        lib.ph_tube_info.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.ph_tube_info.restype = ctypes.c_int
         _cpu_lib = lib
     return _cpu_lib
 
@@ -84,6 +86,7 @@ class VolumeSpec:
     seed: int = 1001
     n_ell: int = 12
     n_cyl: int = 0
+    tube: bool = False      # a cylindrical sample container around the objects
 
     @property
     def esize(self) -> int:
@@ -130,10 +133,20 @@ def make_params(spec: VolumeSpec) -> ctypes.Array:
     lib = _cpu()
     buf = (ctypes.c_uint8 * lib.ph_params_size())()
     rc = lib.ph_make_params(spec.nx, spec.ny, spec.nz, spec.bits, spec.esize, spec.seed,
-                            spec.n_ell, spec.n_cyl, ctypes.addressof(buf))
+                            spec.n_ell, spec.n_cyl, int(spec.tube), ctypes.addressof(buf))
     if rc != 0:
         raise ValueError(f"ph_make_params failed for {spec}")
     return buf
+
+
+def tube_geometry(spec: VolumeSpec):
+    """(axis x, axis y, inner radius, outer radius) of the container in voxel-index
+    coordinates, or None for a volume without one."""
+    P = make_params(spec)
+    out = np.zeros(4, np.float64)
+    if not _cpu().ph_tube_info(ctypes.addressof(P), out.ctypes.data_as(ctypes.c_void_p)):
+        return None
+    return tuple(float(v) for v in out)
 
 
 def generate_cpu(spec: VolumeSpec, box=None) -> np.ndarray:

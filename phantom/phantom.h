@@ -15,8 +15,13 @@
  *                from every face
  *   cylinders    "appendages": radius U(1.5,4), length U(50,400), starting on
  *                an ellipsoid surface and pointing outwards, clipped to the box
+ *   container    optional: a z-aligned cylindrical shell (the sample
+ *                container, Sec. III "Container Removal") around the box's
+ *                centre, outer radius 0.46 min(nx, ny), wall max(3, 0.03
+ *                min(nx, ny)) voxels, intensity U{60..75}; the ellipsoids are
+ *                then placed inside its inner radius
  *   a voxel takes the intensity of the last primitive that contains its
- *   centre (ellipsoids first, then cylinders, in index order)
+ *   centre (container, then ellipsoids, then cylinders, in index order)
  *   grey values are scaled by 2^(bits-8) and clamped to [0, 2^bits - 1].
  * Randomness: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) used as a
  * counter-based generator, output k of the stream seeded with s being
@@ -56,6 +61,9 @@ typedef struct {
     int32_t bits, esize;
     int32_t n_ell, n_cyl;
     int32_t bg_mean, bg_sd, obj_sd, pad;
+    int32_t tube, tube_intensity;   /* container shell (tube != 0) */
+    float tube_c[2];                /* axis position (x, y) */
+    float tube_r2_in, tube_r2_out;  /* squared inner / outer radius */
     ph_ellipsoid ell[PH_MAX_ELL];
     ph_cylinder cyl[PH_MAX_CYL];
 } ph_params;
@@ -133,8 +141,15 @@ PH_HD int ph_in_cylinder(const ph_cylinder *c, float x, float y, float z)
     return perp2 <= c->r2;
 }
 
+PH_HD int ph_in_tube(const ph_params *P, float x, float y)
+{
+    float dx = ph_sub(x, P->tube_c[0]), dy = ph_sub(y, P->tube_c[1]);
+    float d2 = ph_add(ph_mul(dx, dx), ph_mul(dy, dy));
+    return P->tube && d2 >= P->tube_r2_in && d2 <= P->tube_r2_out;
+}
+
 /* Grey value of voxel (x, y, z) given the index of the primitive that owns it
- * (-1 = background; ellipsoids 0..n_ell-1, cylinders n_ell..). */
+ * (-1 = background, -2 = container; ellipsoids 0..n_ell-1, cylinders n_ell..). */
 PH_HD uint32_t ph_grey(const ph_params *P, int64_t x, int64_t y, int64_t z, int owner)
 {
     uint64_t idx = (uint64_t)((z * P->ny + y) * P->nx + x);
@@ -145,7 +160,8 @@ PH_HD uint32_t ph_grey(const ph_params *P, int64_t x, int64_t y, int64_t z, int 
              (int64_t)((h >> 32) & 0xffff) + (int64_t)(h >> 48);
     }
     int64_t base, sd;
-    if (owner < 0) { base = P->bg_mean; sd = P->bg_sd; }
+    if (owner == -1) { base = P->bg_mean; sd = P->bg_sd; }
+    else if (owner == -2) { base = P->tube_intensity; sd = P->obj_sd; }
     else if (owner < P->n_ell) { base = P->ell[owner].intensity; sd = P->obj_sd; }
     else { base = P->cyl[owner - P->n_ell].intensity; sd = P->obj_sd; }
     int64_t scale = (int64_t)1 << (P->bits - 8);
@@ -161,7 +177,7 @@ extern "C" {
 /* Fill *P for a volume; returns 0 or -1 on bad arguments.  Implemented once,
  * in phantom_params.c, and linked into both builds. */
 int ph_make_params(int64_t nx, int64_t ny, int64_t nz, int32_t bits, int32_t esize,
-                   uint64_t seed, int32_t n_ell, int32_t n_cyl, ph_params *P);
+                   uint64_t seed, int32_t n_ell, int32_t n_cyl, int32_t tube, ph_params *P);
 #ifdef __cplusplus
 }
 #endif

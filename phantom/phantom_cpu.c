@@ -5,12 +5,25 @@
  * test only the primitives whose bounding boxes touch them; the per-voxel
  * value comes from phantom.h and matches the GPU writer byte for byte.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 
 #include "phantom.h"
 
 int ph_params_size(void) { return (int)sizeof(ph_params); }
+
+/* The container of *P in voxel-index coordinates (voxel centres sit at index
+ * + 1/2): axis (x, y), inner and outer radius; returns 0 when there is none. */
+int ph_tube_info(const ph_params *P, double out[4])
+{
+    if (!P || !P->tube) return 0;
+    out[0] = (double)P->tube_c[0] - 0.5;
+    out[1] = (double)P->tube_c[1] - 0.5;
+    out[2] = sqrt((double)P->tube_r2_in);
+    out[3] = sqrt((double)P->tube_r2_out);
+    return 1;
+}
 
 static int brick_overlaps(const float lo[3], const float hi[3], int64_t bx0, int64_t by0,
                           int64_t bz0, int64_t bx1, int64_t by1, int64_t bz1)
@@ -48,7 +61,7 @@ int ph_generate_cpu(const ph_params *P, int64_t x0, int64_t x1, int64_t y0, int6
                     for (int64_t y = by; y < ey; ++y)
                         for (int64_t x = bx; x < ex; ++x) {
                             float fx = (float)x + 0.5f, fy = (float)y + 0.5f, fz = (float)z + 0.5f;
-                            int owner = -1;
+                            int owner = ph_in_tube(P, fx, fy) ? -2 : -1;
                             for (int q = 0; q < nc; ++q) {
                                 int p = cand[q];
                                 if (p < P->n_ell) {

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(PH_BX) ph_kernel(const ph_params *__restrict__
     for (int64_t z = bz; z < ez; ++z)
         for (int64_t y = by; y < ey; ++y) {
             const float fy = (float)y + 0.5f, fz = (float)z + 0.5f;
-            int owner = -1;
+            int owner = ph_in_tube(P, fx, fy) ? -2 : -1;
             for (int w = 0; w < PH_MASK_WORDS; ++w) {
                 unsigned m = mask[w];
                 while (m) {

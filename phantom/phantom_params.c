@@ -31,7 +31,7 @@ static void unit_vec(ph_stream *st, double v[3])
 }
 
 int ph_make_params(int64_t nx, int64_t ny, int64_t nz, int32_t bits, int32_t esize,
-                   uint64_t seed, int32_t n_ell, int32_t n_cyl, ph_params *P)
+                   uint64_t seed, int32_t n_ell, int32_t n_cyl, int32_t tube, ph_params *P)
 {
     const double PI = 3.14159265358979323846;
     if (!P || nx <= 0 || ny <= 0 || nz <= 0 || bits < 8 || bits > 16) return -1;
@@ -48,6 +48,23 @@ int ph_make_params(int64_t nx, int64_t ny, int64_t nz, int32_t bits, int32_t esi
     double nmin = fmin(N[0], fmin(N[1], N[2]));
     double scale = nmin / 256.0;
     double a_cap = floor(nmin / 2.0) - 5.0;   /* bounding radius that still fits */
+    double tube_in = 0.0, tcx = 0.0, tcy = 0.0;
+    if (tube) {
+        /* its own stream, so volumes without a container keep their draws */
+        ph_stream ts = {seed * 0x9e3779b97f4a7c15ULL + 0x2545f4914f6cdd1dULL, 0};
+        double nxy = fmin(N[0], N[1]);
+        double r_out = 0.46 * nxy, wall = fmax(3.0, 0.03 * nxy);
+        tcx = N[0] / 2.0 + (uni(&ts) - 0.5) * 0.06 * nxy;
+        tcy = N[1] / 2.0 + (uni(&ts) - 0.5) * 0.06 * nxy;
+        tube_in = r_out - wall;
+        P->tube = 1;
+        P->tube_intensity = 60 + (int32_t)floor(16.0 * uni(&ts));
+        P->tube_c[0] = (float)tcx;
+        P->tube_c[1] = (float)tcy;
+        P->tube_r2_in = (float)(tube_in * tube_in);
+        P->tube_r2_out = (float)(r_out * r_out);
+        a_cap = fmin(a_cap, floor(tube_in / 2.0) - 4.0);
+    }
 
     int ne = 0;
     for (int e = 0; e < n_ell && a_cap >= 2.0; ++e) {
@@ -64,6 +81,14 @@ int ph_make_params(int64_t nx, int64_t ny, int64_t nz, int32_t bits, int32_t esi
         for (int i = 0; i < 3; ++i) {
             double lo = rb + 4.0, hi = N[i] - rb - 4.0;
             c[i] = hi > lo ? lo + (hi - lo) * uni(&st) : N[i] / 2.0;
+        }
+        if (tube) {
+            /* centre the ellipsoid inside the container: a point of the disk
+             * of radius tube_in - rb - 4 around the axis */
+            double rr = fmax(0.0, tube_in - rb - 4.0) * sqrt(uni(&st));
+            double ph = 2.0 * PI * uni(&st);
+            c[0] = tcx + rr * cos(ph);
+            c[1] = tcy + rr * sin(ph);
         }
         int32_t inten = 80 + (int32_t)floor(141.0 * uni(&st));
         ph_ellipsoid *E = &P->ell[ne++];
