@@ -9,7 +9,7 @@ steps.  The input (14.6 GB) is larger than L2, so no flush is needed between
 steps.  Multi-GPU runs are independent replicas (weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mctp|reference]
-                  [--workload full|mid|slab|small|batch|serve|fit]
+                  [--workload full|mid|slab|small|batch|serve|fit|thresholds]
 
 --workload batch: 64 u8 phantoms with axes ~ U{384..1024} (22 GB resident),
 each through histogram, Otsu and a 256^3 slicemap, then 12 views of each at
@@ -28,6 +28,11 @@ at 24 views 512^2 (azimuth 15k deg, elevation alternating +-20 deg) as FP32
 targets; a 128^3 FP32 reduced volume (started from the 128^3 slicemap level)
 and its 256-entry LUT are fitted by Adam through the adjoint ray march; a
 step is one iteration (forward, loss, adjoint, two Adam updates).
+
+--workload thresholds: the Otsu / ITS comparison of Fig. 5 on five u8
+phantoms with a sample container, sized like Table II's datasets A-E: the
+histogram, Otsu and ITS on the GPU (and the oracle's Otsu and ITS on the host),
+before and after container removal.
 """
 from __future__ import annotations
 
@@ -68,6 +73,15 @@ def workload(name: str):
                     az_step=10.0, desc="slab (profiling): u16 12-bit 2016x2016x224 phantom (1.8 GB) with the full "
                                        "workload's footprints, 4096 bins, Otsu, levels 512x512x64/256x256x32/"
                                        "128x128x16, 4 views 1024x1024")
+    if name == "thresholds":
+        dims = [(1536, 1536, 1152), (1536, 1536, 1152), (2016, 2016, 2016), (2016, 2016, 1692), (1968, 1968, 1456)]
+        specs = [phantom.VolumeSpec(x, y, z, bits=8, seed=6000 + i, n_ell=12, tube=True)
+                 for i, (x, y, z) in enumerate(dims)]
+        return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=1, nviews=1,
+                    size=512, az_step=0.0,
+                    desc="thresholds: 5 u8 phantoms with a container, sized like Table II A-E (1536^2x1152 x2, "
+                         "2016^2x2016, 2016^2x1692, 1968^2x1456; %.1f GB), 256 bins; Otsu and ITS before and "
+                         "after container removal" % (sum(sp.nbytes for sp in specs) / 1e9))
     if name == "fit":
         spec = phantom.VolumeSpec(1024, 1024, 1024, bits=8, seed=1004, n_ell=12, n_cyl=0)
         return dict(spec=spec, bits=8, nbins=256, level0=(1024, 1024, 1024), nlevels=4, nviews=24, size=512,
@@ -658,6 +672,79 @@ def run_batch(args, wl):
     return 0
 
 
+def run_thresholds(args, wl):
+    """Fig. 5 analogue: threshold selection times (GPU and host oracle) and results."""
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    oracle.build()
+    stream = torch.cuda.current_stream(dev)
+
+    def gpu_ms(fn, reps=50):
+        fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def cpu_ms(fn, reps=200):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        return (time.perf_counter() - t0) * 1e3 / reps, out
+
+    rows = []
+    total_bytes = 0
+    total_hist_s = 0.0
+    for label, sp in zip("ABCDE", wl["specs"]):
+        vol = torch.empty(sp.shape, dtype=torch.uint8, device=dev)
+        phantom.generate_gpu(sp, vol)
+        total_bytes += sp.nbytes
+        row = dict(dataset=label, dims=[sp.nx, sp.ny, sp.nz], gbytes=sp.nbytes / 1e9)
+        for stage in ("raw", "container_removed"):
+            if stage == "container_removed":
+                n = min(sp.nx, sp.ny)
+                found = mctp.find_container(vol, 8, 0, 40, n // 8, n // 2, max(4, n // 32))
+                mctp.mask_container(vol, 8, found["circle"], 2, out=vol)
+                row["container_circle"] = [int(v) for v in found["circle"].cpu().tolist()]
+            hist = torch.empty(256, dtype=torch.uint64, device=dev)
+            ov = torch.empty(1, dtype=torch.uint64, device=dev)
+            h_ms = gpu_ms(lambda: mctp.build_histogram(vol, 8, 256, hist=hist, overflow=ov), reps=5)
+            total_hist_s += h_ms / 1e3
+            keep = torch.empty(256, dtype=torch.uint8, device=dev)
+            res = torch.empty(4, dtype=torch.int32, device=dev)
+            otsu_ms = gpu_ms(lambda: mctp.select_threshold(hist, 256, "otsu", keep=keep, result=res))
+            T_otsu = int(res[0].item())
+            its_ms = gpu_ms(lambda: mctp.select_threshold(hist, 256, "its", keep=keep, result=res))
+            T_its, its_iters = int(res[0].item()), int(res[1].item())
+            h_np = hist.cpu().numpy()
+            o_ms, (To, _) = cpu_ms(lambda: oracle.otsu(h_np))
+            i_ms, (Ti, it_i, conv, _) = cpu_ms(lambda: oracle.its(h_np))
+            assert To == T_otsu and Ti == T_its
+            row[stage] = dict(histogram_ms=h_ms, histogram_gbs=sp.nbytes / (h_ms / 1e3) / 1e9,
+                              otsu=dict(T=T_otsu, gpu_ms=otsu_ms, host_oracle_ms=o_ms),
+                              its=dict(T=T_its, iterations=its_iters, gpu_ms=its_ms, host_oracle_ms=i_ms))
+        rows.append(row)
+        del vol
+        torch.cuda.empty_cache()
+    line = dict(metric=METRIC, value=total_bytes / total_hist_s / 1e9, unit="histogram GB/s", n_gpus=1, steps=1,
+                warmup=1, ms_per_step=total_hist_s * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="u8", data="synthetic", config=dict(workload=wl["desc"]), thresholds=rows,
+                note="Fig. 5 analogue: Otsu sweeps all 256 bins, ITS stops once converged; times per selection")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fit(args, wl):
     """The differentiable workload: Adam iterations fitting a 128^3 volume and its LUT."""
     import torch
@@ -907,7 +994,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "mid", "slab", "small", "batch", "serve", "fit"])
+    ap.add_argument("--workload", default="full",
+                    choices=["full", "mid", "slab", "small", "batch", "serve", "fit", "thresholds"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = workload(args.workload)
@@ -919,6 +1007,8 @@ def main():
         return run_serve(args, wl)
     if args.workload == "fit":
         return run_fit(args, wl)
+    if args.workload == "thresholds":
+        return run_thresholds(args, wl)
     return run_gpu(args, wl)
 
 

@@ -427,6 +427,41 @@ int mctp_adam_step(float *param, const float *grad, float *m, float *v, int64_t 
 int mctp_image_entropy(const float *rgba, const mctp_view *views, int32_t nviews, uint64_t *hist,
                        double *entropy, int32_t *best, void *stream);
 
+/*
+ * Container removal (Sec. III, Container Removal): find the sample
+ * container's circle on slice z (the top slice), then zero every voxel
+ * outside it in every slice.  The circle is found by a Hough circle transform
+ * in the manner the paper cites (centre by votes along gradient lines, radius
+ * by a histogram of edge distances), refined by least-squares circle fits:
+ *   1. [1 4 6 4 1]^2 smoothing (borders clamped), integer Sobel gradient;
+ *      edge pixels have |g|^2 >= (256 thr)^2 (thr in grey units);
+ *   2. each edge pixel votes, against its gradient, at distances rmin..rmax
+ *      into cells of cell x cell pixels (acc, ceil(ny/cell) x ceil(nx/cell));
+ *      the fullest cell (first in row-major order on ties) is the centre;
+ *   3. histogram (rhist, rmax + 1 bins) of the rounded distances of the edge
+ *      pixels whose gradient points away from the centre; its mode (smallest
+ *      on ties) is the radius;
+ *   4. three least-squares circle fits over those pixels within 2 cell + 3,
+ *      cell + 3 and 3 pixels of the current circle.
+ * The inner wall of a bright container around darker air is found.
+ *   acc, rhist  device uint32 outputs (vote counts)
+ *   workspace   device, mctp_container_workspace(nx, ny) bytes, 256-byte aligned
+ *   circle      device int32[3]: centre x, y (rounded) and radius (floor); radius
+ *               -1 when no edge pixel votes for a circle in [rmin, rmax]
+ *   fit         device double[3] or NULL: the unrounded circle
+ * Errors: MCTP_EINVAL (bad arguments, nx or ny < 3), MCTP_ESIZE (workspace).
+ */
+size_t mctp_container_workspace(int64_t nx, int64_t ny);
+int mctp_find_container(const void *vol, const mctp_volume_desc *d, int64_t z, int64_t thr, int32_t rmin,
+                        int32_t rmax, int32_t cell, uint32_t *acc, uint32_t *rhist, void *workspace,
+                        size_t workspace_bytes, int32_t *circle, double *fit, void *stream);
+
+/* out = in with every voxel (x, y, z) where (x - cx)^2 + (y - cy)^2 >
+ * max(r - margin, 0)^2 set to 0, (cx, cy, r) = circle (device int32[3], e.g.
+ * from mctp_find_container); r < 0 keeps everything.  out may equal in. */
+int mctp_mask_container(const void *in, const mctp_volume_desc *d, const int32_t *circle, int32_t margin,
+                        void *out, void *stream);
+
 /* Default atlas grid for mz slices: tiles_x = 2^ceil(log2 sqrt(mz)),
  * tiles_y = ceil(mz / tiles_x).  Returns MCTP_EINVAL for mz < 1. */
 int mctp_default_tiles(int32_t mz, int32_t *tiles_x, int32_t *tiles_y);

@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import MctpError  # noqa: F401
 
 __all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
-           "render_batch", "render_batch_workspace", "render_batch_static", "BatchTuning", "image_entropy", "Slicemap", "View", "default_tiles",
+           "render_batch", "render_batch_workspace", "render_batch_static", "BatchTuning", "image_entropy",
+           "find_container", "mask_container", "Slicemap", "View", "default_tiles",
            "atlas_bytes", "version", "MctpError"]
 
 _DTYPES = {torch.uint8: (_lib.MCTP_U8, 1), torch.uint16: (_lib.MCTP_U16, 2), torch.int16: (_lib.MCTP_U16, 2)}
@@ -336,3 +337,39 @@ def image_entropy(flat: torch.Tensor, views, hist: torch.Tensor | None = None, e
     _lib.check(_lib.load().mctp_image_entropy(_ptr(flat), view_array(views), n, _ptr(hist), _ptr(entropy), _ptr(best),
                                               _stream(stream)), "mctp_image_entropy")
     return hist, entropy, best
+
+
+def find_container(vol: torch.Tensor, bits: int, z: int = 0, thr: int = 40, rmin: int | None = None,
+                   rmax: int | None = None, cell: int | None = None, stream=None):
+    """Container circle on slice z -> dict(circle int32[3], fit float64[3], acc, rhist) on the device."""
+    _cuda(vol, "vol")
+    d = volume_desc(vol, bits)
+    nz, ny, nx = vol.shape
+    n = min(nx, ny)
+    rmin = n // 8 if rmin is None else rmin
+    rmax = n // 2 if rmax is None else rmax
+    cell = max(4, n // 32) if cell is None else cell
+    dev = vol.device
+    lib = _lib.load()
+    acc = torch.empty((-(-ny // cell), -(-nx // cell)), dtype=torch.int32, device=dev)
+    rhist = torch.empty(rmax + 1, dtype=torch.int32, device=dev)
+    nb = lib.mctp_container_workspace(nx, ny)
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+    circle = torch.empty(3, dtype=torch.int32, device=dev)
+    fit = torch.empty(3, dtype=torch.float64, device=dev)
+    _lib.check(lib.mctp_find_container(_ptr(vol), ctypes.byref(d), z, thr, rmin, rmax, cell, _ptr(acc), _ptr(rhist),
+                                       _ptr(ws), ws.numel(), _ptr(circle), _ptr(fit), _stream(stream)),
+               "mctp_find_container")
+    return dict(circle=circle, fit=fit, acc=acc, rhist=rhist)
+
+
+def mask_container(vol: torch.Tensor, bits: int, circle: torch.Tensor, margin: int = 2,
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """vol with everything outside the container circle zeroed (out may be vol)."""
+    _cuda(vol, "vol")
+    d = volume_desc(vol, bits)
+    if out is None:
+        out = torch.empty_like(vol)
+    _lib.check(_lib.load().mctp_mask_container(_ptr(vol), ctypes.byref(d), _ptr(circle), margin, _ptr(out),
+                                               _stream(stream)), "mctp_mask_container")
+    return out

@@ -102,6 +102,10 @@ EXPORTS = {
     "mctp_adam_step": ([C_VP, C_VP, C_VP, C_VP, C_I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                         ctypes.c_float, C_I32, ctypes.c_float, ctypes.c_float, C_VP], ctypes.c_int),
     "mctp_image_entropy": ([C_VP, ctypes.POINTER(ViewDesc), C_I32, C_VP, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_container_workspace": ([C_I64, C_I64], ctypes.c_size_t),
+    "mctp_find_container": ([C_VP, ctypes.POINTER(VolumeDesc), C_I64, C_I64, C_I32, C_I32, C_I32, C_VP, C_VP, C_VP,
+                             ctypes.c_size_t, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_mask_container": ([C_VP, ctypes.POINTER(VolumeDesc), C_VP, C_I32, C_VP, C_VP], ctypes.c_int),
     "mctp_default_tiles": ([C_I32, ctypes.POINTER(C_I32), ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_atlas_bytes": ([C_I32, C_I32, C_I32, C_I32, C_I32], ctypes.c_size_t),
     "mctp_maxgrid_bytes": ([C_I32, C_I32, C_I32], ctypes.c_size_t),

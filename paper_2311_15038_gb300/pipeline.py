@@ -9,7 +9,8 @@ from dataclasses import dataclass
 
 import torch
 
-from . import Slicemap, View, build_histogram, build_slicemap, image_entropy, render_views, select_threshold
+from . import (Slicemap, View, build_histogram, build_slicemap, find_container, image_entropy, mask_container,
+               render_views, select_threshold)
 
 
 @dataclass
@@ -24,6 +25,9 @@ class PreviewConfig:
     topslab: int = 3                        # slices of the top slab (topslab mode)
     alpha_stop: float = 0.99
     explicit_T: int = 0
+    container: bool = False                 # remove the sample container first (Hough circle on slice 0)
+    container_thr: int = 40                 # edge threshold in 8-bit grey units
+    container_margin: int = 2               # voxels kept inside the found inner wall
 
 
 def turntable(n: int, size: int, level: int = 0, step: float = 0.5, elevation: float = 0.0,
@@ -47,6 +51,11 @@ class PreviewPipeline:
         total = sum(v.width * v.height * 4 for v in cfg.views)
         self.images = torch.empty(max(total, 4), dtype=torch.float32, device=self.device)
         self.samples = torch.empty(1, dtype=torch.uint64, device=self.device)
+        self.masked = None
+        if cfg.container:
+            nx, ny, nz = cfg.src_dims
+            self.masked = torch.empty((nz, ny, nx), dtype=dtype, device=self.device)
+            self.circle = None
         nv = max(len(cfg.views), 1)
         self.image_hist = torch.empty((nv, 256), dtype=torch.uint64, device=self.device)
         self.entropy = torch.empty(nv, dtype=torch.float64, device=self.device)
@@ -57,6 +66,11 @@ class PreviewPipeline:
         c = self.cfg
         mark = timer or (lambda name: None)
         keep = None
+        if c.container:
+            mark("container")
+            thr = c.container_thr << (c.bits - 8) if c.bits > 8 else c.container_thr
+            self.circle = find_container(vol, c.bits, 0, thr, stream=self.stream)["circle"]
+            vol = mask_container(vol, c.bits, self.circle, c.container_margin, self.masked, self.stream)
         mark("histogram")
         if c.mode == "topslab":
             build_histogram(vol, c.bits, c.nbins, 0, c.topslab, self.hist, self.overflow, self.stream)
