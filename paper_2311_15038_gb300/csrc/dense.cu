@@ -223,6 +223,18 @@ __global__ void __launch_bounds__(kThreads) dense_backward_kernel(const __grid_c
         }
         // pass 2: segments last to first, each re-marched for its T_k, then walked back
         float RC0 = 0.f, RC1 = 0.f, RC2 = 0.f, RA = 0.f;
+        int run_j = -1;
+        float run_lo[4] = {0.f, 0.f, 0.f, 0.f}, run_hi[4] = {0.f, 0.f, 0.f, 0.f};
+        auto flush_run = [&]() {
+            if (run_j < 0) return;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                if (run_lo[ch] != 0.0f) atomicAdd(&glut[4 * run_j + ch], run_lo[ch]);
+                if (run_hi[ch] != 0.0f) atomicAdd(&glut[4 * (run_j + 1) + ch], run_hi[ch]);
+                run_lo[ch] = 0.f;
+                run_hi[ch] = 0.f;
+            }
+        };
         for (int seg = (ne - 1) / kSeg; seg >= 0; --seg) {
             const int k0 = seg * kSeg, k1 = min(k0 + kSeg, ne);
             float T[kSeg];
@@ -249,13 +261,18 @@ __global__ void __launch_bounds__(kThreads) dense_backward_kernel(const __grid_c
                 RA = fmaf(a, 1.0f - RA, RA);
                 const float4 e0 = lut[l.j], e1 = lut[l.j + 1];
                 const float de[4] = {e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w};
+                // LUT gradient: consecutive samples of a ray mostly fall between the
+                // same two entries, so it is summed in registers until the entry pair
+                // changes and only then added to the CTA's table
+                if (l.j != run_j) {
+                    flush_run();
+                    run_j = l.j;
+                }
                 float gv = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
-                    if (ge[ch] != 0.0f) {
-                        atomicAdd(&glut[4 * l.j + ch], (1.0f - l.fl) * ge[ch]);
-                        atomicAdd(&glut[4 * (l.j + 1) + ch], l.fl * ge[ch]);
-                    }
+                    run_lo[ch] = fmaf(1.0f - l.fl, ge[ch], run_lo[ch]);
+                    run_hi[ch] = fmaf(l.fl, ge[ch], run_hi[ch]);
                     gv = fmaf(ge[ch], de[ch], gv);
                 }
                 gv *= nl1;
@@ -274,6 +291,7 @@ __global__ void __launch_bounds__(kThreads) dense_backward_kernel(const __grid_c
                 }
             }
         }
+        flush_run();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * P.nlut; i += blockDim.x)

@@ -6,7 +6,8 @@
 // 709 luminance (0.2126 R + 0.7152 G) + 0.0722 B in FP32 (one rounding per
 // operation, this order), clamped to [0, 1], quantised as floor(lum*255 + 0.5).
 // Histograms: per-warp shared sub-histograms, one block row per view; H in
-// FP64 from the counts, then the argmax (lowest view index on ties).
+// FP64 from the counts, one block per view, then the argmax (lowest view
+// index on ties).
 #include <algorithm>
 
 #include "mctp_internal.cuh"
@@ -55,46 +56,55 @@ __global__ void __launch_bounds__(kEntThreads) image_hist_kernel(const __grid_co
     }
 }
 
-// one block: H of every view (FP64), then the argmax
-__global__ void __launch_bounds__(kEntThreads) entropy_kernel(const unsigned long long *__restrict__ hist, int nviews,
-                                                              double *__restrict__ H, int32_t *__restrict__ best)
+// One block per view: H in FP64 from the view's 256 counts, one bin per
+// thread, reduced in a fixed order (warp shuffles, then warps in order).
+__global__ void __launch_bounds__(kEntThreads) entropy_kernel(const unsigned long long *__restrict__ hist,
+                                                              double *__restrict__ H)
 {
+    static_assert(kEntThreads == 256, "one thread per bin");
+    __shared__ unsigned long long sh_t[kWarps];
     __shared__ double sh_h[kWarps];
-    __shared__ double best_h;
-    __shared__ int best_v;
-    if (threadIdx.x == 0) { best_h = -1.0; best_v = -1; }
-    for (int v = 0; v < nviews; ++v) {
-        __syncthreads();
-        const unsigned long long *h = hist + int64_t(v) * 256;
-        // total count
-        unsigned long long tot = 0;
-        for (int b = threadIdx.x; b < 256; b += blockDim.x) tot += h[b];
+    const int v = blockIdx.x, b = threadIdx.x, lane = b & 31, w = b >> 5;
+    const unsigned long long c = hist[int64_t(v) * 256 + b];
+    unsigned long long tot = c;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        __shared__ unsigned long long sh_t[kWarps];
-        if ((threadIdx.x & 31) == 0) sh_t[threadIdx.x >> 5] = tot;
-        __syncthreads();
-        tot = 0;
-        for (int w = 0; w < kWarps; ++w) tot += sh_t[w];
-        double acc = 0.0;
-        for (int b = threadIdx.x; b < 256; b += blockDim.x)
-            if (h[b]) {
-                const double p = double(h[b]) / double(tot);
-                acc -= p * log2(p);
-            }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) sh_h[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < kWarps; ++w) s += sh_h[w];  // fixed order
-            H[v] = s;
-            if (s > best_h) { best_h = s; best_v = v; }
-        }
-    }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) sh_t[w] = tot;
     __syncthreads();
-    if (threadIdx.x == 0 && best) *best = best_v;
+    tot = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) tot += sh_t[k];
+    double term = 0.0;
+    if (c) {
+        const double p = __ddiv_rn(double(c), double(tot));
+        term = -__dmul_rn(p, log2(p));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term = __dadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
+    if (lane == 0) sh_h[w] = term;
+    __syncthreads();
+    if (b == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) sum = __dadd_rn(sum, sh_h[k]);
+        H[v] = sum;
+    }
+}
+
+// The view with the largest H (lowest index on ties).
+__global__ void __launch_bounds__(32) best_view_kernel(const double *__restrict__ H, int nviews, int32_t *best)
+{
+    double bh = -1.0;
+    int bv = -1;
+    for (int v = threadIdx.x; v < nviews; v += 32)
+        if (H[v] > bh) { bh = H[v]; bv = v; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oh = __shfl_xor_sync(0xffffffffu, bh, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        if (ov >= 0 && (bv < 0 || oh > bh || (oh == bh && ov < bv))) { bh = oh; bv = ov; }
+    }
+    if (threadIdx.x == 0) *best = bv;
 }
 
 }  // namespace
@@ -138,7 +148,10 @@ extern "C" int mctp_image_entropy(const float *rgba, const mctp_view *views, int
         const int rc = launch_status();
         if (rc != MCTP_OK) return rc;
     }
-    entropy_kernel<<<1, kEntThreads, 0, s>>>(reinterpret_cast<const unsigned long long *>(hist), nviews, entropy,
-                                              best);
+    entropy_kernel<<<unsigned(nviews), kEntThreads, 0, s>>>(reinterpret_cast<const unsigned long long *>(hist),
+                                                             entropy);
+    int rc = launch_status();
+    if (rc != MCTP_OK || !best) return rc;
+    best_view_kernel<<<1, 32, 0, s>>>(entropy, nviews, best);
     return launch_status();
 }

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_prep_kernel(const __grid_
 }
 
 template <typename T, bool kLutShared>
-__global__ void __launch_bounds__(kBatchThreads, 3) render_batch_kernel(const __grid_constant__ BatchArgs P)
+__global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __grid_constant__ BatchArgs P)
 {
     extern __shared__ __align__(16) float4 slut[];
     if (kLutShared) {
