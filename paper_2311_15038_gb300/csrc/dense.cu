@@ -21,7 +21,9 @@
 // last to first, is re-marched forward from its checkpoint to recover its
 // T_k (no division by T, so no loss of accuracy when T is small) and then
 // walked backward.  The LUT gradient is accumulated per CTA in shared memory;
-// the volume gradient is scattered with trilinear weights by atomic adds.
+// the volume gradient is scattered with trilinear weights by atomic adds.  Both
+// are first summed in registers over runs of consecutive samples that touch the
+// same table entries / corner voxels.
 #include "render_common.cuh"
 
 namespace mctp {
@@ -225,6 +227,19 @@ __global__ void __launch_bounds__(kThreads) dense_backward_kernel(const __grid_c
         float RC0 = 0.f, RC1 = 0.f, RC2 = 0.f, RA = 0.f;
         int run_j = -1;
         float run_lo[4] = {0.f, 0.f, 0.f, 0.f}, run_hi[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t cell_o = 0xffffffffu, cell_dx = 0, cell_dy = 0, cell_dz = 0;
+        float cw[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        auto flush_cell = [&]() {
+            if (cell_o == 0xffffffffu) return;
+            float *q = P.grad_vol + cell_o;
+            const uint32_t off[8] = {0u, cell_dx, cell_dy, cell_dy + cell_dx, cell_dz, cell_dz + cell_dx,
+                                     cell_dz + cell_dy, cell_dz + cell_dy + cell_dx};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (cw[c] != 0.0f) atomicAdd(q + off[c], cw[c]);
+                cw[c] = 0.f;
+            }
+        };
         auto flush_run = [&]() {
             if (run_j < 0) return;
 #pragma unroll
@@ -277,21 +292,30 @@ __global__ void __launch_bounds__(kThreads) dense_backward_kernel(const __grid_c
                 }
                 gv *= nl1;
                 if (gv != 0.0f && tp.raw > 0.0f && tp.raw < 1.0f) {
-                    float *q = P.grad_vol + tp.o000;
+                    // the volume gradient is summed in registers while consecutive
+                    // samples share the same eight corner voxels
+                    if (tp.o000 != cell_o || tp.dx != cell_dx || tp.dy != cell_dy || tp.dz != cell_dz) {
+                        flush_cell();
+                        cell_o = tp.o000;
+                        cell_dx = tp.dx;
+                        cell_dy = tp.dy;
+                        cell_dz = tp.dz;
+                    }
                     const float wx1 = tp.fx, wx0 = 1.0f - tp.fx, wy1 = tp.fy, wy0 = 1.0f - tp.fy;
                     const float wz1 = tp.fz * gv, wz0 = (1.0f - tp.fz) * gv;
-                    atomicAdd(q, wx0 * wy0 * wz0);
-                    atomicAdd(q + tp.dx, wx1 * wy0 * wz0);
-                    atomicAdd(q + tp.dy, wx0 * wy1 * wz0);
-                    atomicAdd(q + tp.dy + tp.dx, wx1 * wy1 * wz0);
-                    atomicAdd(q + tp.dz, wx0 * wy0 * wz1);
-                    atomicAdd(q + tp.dz + tp.dx, wx1 * wy0 * wz1);
-                    atomicAdd(q + tp.dz + tp.dy, wx0 * wy1 * wz1);
-                    atomicAdd(q + tp.dz + tp.dy + tp.dx, wx1 * wy1 * wz1);
+                    cw[0] = fmaf(wx0 * wy0, wz0, cw[0]);
+                    cw[1] = fmaf(wx1 * wy0, wz0, cw[1]);
+                    cw[2] = fmaf(wx0 * wy1, wz0, cw[2]);
+                    cw[3] = fmaf(wx1 * wy1, wz0, cw[3]);
+                    cw[4] = fmaf(wx0 * wy0, wz1, cw[4]);
+                    cw[5] = fmaf(wx1 * wy0, wz1, cw[5]);
+                    cw[6] = fmaf(wx0 * wy1, wz1, cw[6]);
+                    cw[7] = fmaf(wx1 * wy1, wz1, cw[7]);
                 }
             }
         }
         flush_run();
+        flush_cell();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * P.nlut; i += blockDim.x)
