@@ -6,7 +6,8 @@
 // sub-histograms in shared memory (warp w uses copy w % copies, so warps
 // rarely collide on a counter), reads the slab as 16-byte vectors with four
 // loads in flight per thread, and adds its counters to the u64 global
-// histogram once at the end.  Elements before the first 16-byte boundary and
+// histogram once at the end.  With at most 256 bins the block instead keeps
+// one counter per (bin, lane), which no two lanes of a warp share.  Elements before the first 16-byte boundary and
 // after the last full vector are counted with scalar loads.
 #include <algorithm>
 
@@ -95,6 +96,82 @@ __global__ void __launch_bounds__(kHistThreads)
     }
 }
 
+// At most 256 bins: one counter per (bin, lane) in shared memory, bin-major
+// with the lane fastest, so the 32 atomics of a warp instruction always fall
+// in 32 different banks (peaked histograms, where many lanes share a bin,
+// otherwise serialise).  The warps of a block share the table.
+template <typename T, bool kCheckOverflow>
+__global__ void __launch_bounds__(kHistThreads)
+    hist_lane_kernel(const T *__restrict__ base, int64_t n, int64_t head, int64_t nvec, int shift, uint32_t limit,
+                     int nbins, unsigned long long *__restrict__ hist, unsigned long long *__restrict__ overflow)
+{
+    extern __shared__ uint32_t sh_cols[];  // nbins * 32
+    for (int i = threadIdx.x; i < nbins * 32; i += blockDim.x) sh_cols[i] = 0u;
+    __syncthreads();
+    uint32_t *mine = sh_cols + (threadIdx.x & 31);
+    uint32_t ovf = 0;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
+    constexpr int E = 16 / sizeof(T);
+    const int lane_shift = shift;  // bin = v >> shift; the column word is bin * 32
+    auto count = [&](uint32_t v) {
+        if (kCheckOverflow && v >= limit) {
+            ++ovf;
+            return;
+        }
+        atomicAdd(&mine[(v >> lane_shift) << 5], 1u);
+    };
+    const int64_t tail0 = head + nvec * E;
+    for (int64_t i = tid; i < head; i += nthreads) count(base[i]);
+    for (int64_t i = tail0 + tid; i < n; i += nthreads) count(base[i]);
+    const uint4 *body = reinterpret_cast<const uint4 *>(base + head);
+    int64_t i = tid;
+    for (; i + (kHistUnroll - 1) * nthreads < nvec; i += kHistUnroll * nthreads) {
+        uint4 q[kHistUnroll];
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) q[u] = ld_stream_v4(body + i + u * nthreads);
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (sizeof(T) == 1) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) count((w[k] >> (8 * b)) & 0xffu);
+                } else {
+                    count(w[k] & 0xffffu);
+                    count(w[k] >> 16);
+                }
+            }
+        }
+    }
+    for (; i < nvec; i += nthreads) {
+        const uint4 q = ld_stream_v4(body + i);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sizeof(T) == 1) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) count((w[k] >> (8 * b)) & 0xffu);
+            } else {
+                count(w[k] & 0xffffu);
+                count(w[k] >> 16);
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        uint32_t sum = 0;
+        for (int l = 0; l < 32; ++l) sum += sh_cols[b * 32 + ((l + b) & 31)];  // rotated: no bank conflicts
+        if (sum) atomicAdd(&hist[b], (unsigned long long)sum);
+    }
+    if (kCheckOverflow) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
+        if ((threadIdx.x & 31) == 0 && ovf) atomicAdd(overflow, (unsigned long long)ovf);
+    }
+}
+
 // Bins too many for shared memory (nbins > 16384): count straight into the
 // global u64 histogram.
 template <typename T>
@@ -122,6 +199,24 @@ int launch_hist(const T *base, int64_t n, int bits, int nbins, uint64_t *hist, u
     if (nbins > 16384) {
         int grid = num_sms() * 8;
         hist_global_kernel<T><<<grid, 256, 0, s>>>(base, n, shift, limit, h, ov);
+        return launch_status();
+    }
+    const uintptr_t addr0 = reinterpret_cast<uintptr_t>(base);
+    if (nbins <= 256) {
+        const size_t smem = size_t(nbins) * 32 * 4;
+        int64_t head = int64_t(((16 - (addr0 & 15)) & 15) / sizeof(T));
+        if (head > n) head = n;
+        const int64_t nvec = (n - head) / (16 / int64_t(sizeof(T)));
+        auto kern = check ? hist_lane_kernel<T, true> : hist_lane_kernel<T, false>;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHistThreads, smem);
+        per_sm = std::max(per_sm, 1);
+        int64_t want = (nvec + int64_t(kHistThreads) * kHistUnroll - 1) / (int64_t(kHistThreads) * kHistUnroll);
+        int64_t grid = std::min<int64_t>(int64_t(per_sm) * num_sms(), std::max<int64_t>(want, 1));
+        // every lane column stays below 2^31 counts
+        grid = std::max<int64_t>(grid, (n >> 35) + 1);
+        grid = std::min<int64_t>(grid, 0x7fffffff);
+        kern<<<unsigned(grid), kHistThreads, smem, s>>>(base, n, head, nvec, shift, limit, nbins, h, ov);
         return launch_status();
     }
     // copies: as many private sub-histograms as fit in ~64 KB, up to one per warp

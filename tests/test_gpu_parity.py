@@ -42,6 +42,7 @@ HIST_CASES = [
     ("u8_1bin", (5, 7, 11), 8, 1),
     ("u16_12bit_ovf", (17, 31, 45), 12, 4096),
     ("u16_12bit_512", (17, 31, 45), 12, 512),
+    ("u16_12bit_256_ovf", (19, 33, 47), 12, 256),   # lane-column kernel with the overflow check
     ("u16_16bit_65536", (9, 33, 41), 16, 65536),
 ]
 
