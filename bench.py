@@ -52,7 +52,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ray samples/s + slicemap build HBM GB/s (% of peak); p50/p99 preview latency"
 UNIT = "ray samples/s"
-FP32_FLOPS_PER_SAMPLE = 48       # algorithmic FP32 work of one sample (render roofline)
+# algorithmic FP32 work of one sample: trilinear 21, normalisation 2, LUT coordinate 3, LUT
+# lerps 12, compositing 9, position step 1
+FP32_FLOPS_PER_SAMPLE = 48
 
 
 def workload(name: str):
