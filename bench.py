@@ -711,7 +711,6 @@ def run_thresholds(args, wl):
     for label, sp in zip("ABCDE", wl["specs"]):
         vol = torch.empty(sp.shape, dtype=torch.uint8, device=dev)
         phantom.generate_gpu(sp, vol)
-        total_bytes += sp.nbytes
         row = dict(dataset=label, dims=[sp.nx, sp.ny, sp.nz], gbytes=sp.nbytes / 1e9)
         for stage in ("raw", "container_removed"):
             if stage == "container_removed":
@@ -723,6 +722,7 @@ def run_thresholds(args, wl):
             ov = torch.empty(1, dtype=torch.uint64, device=dev)
             h_ms = gpu_ms(lambda: mctp.build_histogram(vol, 8, 256, hist=hist, overflow=ov), reps=5)
             total_hist_s += h_ms / 1e3
+            total_bytes += sp.nbytes
             keep = torch.empty(256, dtype=torch.uint8, device=dev)
             res = torch.empty(4, dtype=torch.int32, device=dev)
             otsu_ms = gpu_ms(lambda: mctp.select_threshold(hist, 256, "otsu", keep=keep, result=res))
@@ -739,12 +739,42 @@ def run_thresholds(args, wl):
         rows.append(row)
         del vol
         torch.cuda.empty_cache()
-    line = dict(metric=METRIC, value=total_bytes / total_hist_s / 1e9, unit="histogram GB/s", n_gpus=1, steps=1,
+    pk = peaks()
+    gbs = total_bytes / total_hist_s / 1e9
+    sp0 = wl["specs"][0]
+    slab = phantom.generate_cpu(sp0, ((0, sp0.nx), (0, sp0.ny), (0, 256)))
+    t0 = time.perf_counter()
+    oracle.histogram(slab, 8, 256)
+    t_orc = time.perf_counter() - t0
+    line = dict(metric=METRIC, value=gbs, unit="histogram GB/s", n_gpus=1, steps=1,
                 warmup=1, ms_per_step=total_hist_s * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="u8", data="synthetic", config=dict(workload=wl["desc"]), thresholds=rows,
+                roofline=dict(bound="hbm", achieved=gbs, peak=pk["hbm_gbs"], unit="GB/s", frac=gbs / pk["hbm_gbs"],
+                              kernel="hist_lane_kernel", traffic=None, peak_source=pk["source"]),
+                cpu_baseline=dict(value=slab.nbytes / t_orc / 1e9, unit="histogram GB/s", cores=1, kind="oracle",
+                                  sample=f"oracle histogram (C, 1 thread) of 256 slices of dataset A ({slab.nbytes / 1e6:.0f} MB)"),
                 note="Fig. 5 analogue: Otsu sweeps all 256 bins, ITS stops once converged; times per selection")
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fit_oracle_baseline(fit, view, src_dims):
+    """The oracle's forward render and FP64 gradient of the fitted volume on one
+    128 x 128 view of the same geometry; samples of the forward per second of
+    (forward + gradient), the unit of the fit workload's value."""
+    import oracle
+    oracle.build()
+    vol = fit.vol.double().cpu().numpy()
+    lut = fit.lut.double().cpu().numpy()
+    w = h = 128
+    t0 = time.perf_counter()
+    _, ns = oracle.render_dense(vol, src_dims, lut, view.azimuth_deg, view.elevation_deg, w, h, view.step, 0.99)
+    g = np.ones((h, w, 4))
+    oracle.render_dense_grad(vol, src_dims, lut, view.azimuth_deg, view.elevation_deg, w, h, g, view.step, 0.99)
+    dt = time.perf_counter() - t0
+    return dict(value=float(ns.sum()) / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"oracle (C, 1 thread) FP64 forward + reverse-mode gradient of one 128x128 view "
+                       f"({int(ns.sum())} samples) of the fitted 128^3 volume, {dt:.1f} s")
 
 
 def run_fit(args, wl):
@@ -869,6 +899,7 @@ def run_fit(args, wl):
         roofline=dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
                       kernel="dense_forward_kernel", traffic=None,
                       peak_source="FP32 issue rate at the maximum SM clock"),
+        cpu_baseline=fit_oracle_baseline(fit, fviews[0], (spec.nx, spec.ny, spec.nz)),
         gpu_launches=5 * args.steps,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
         e2e=dict(value=samples_fwd / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=4,
@@ -880,6 +911,24 @@ def run_fit(args, wl):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def serve_oracle_baseline(sm, lut):
+    """The oracle render of 32768 rays of one 512 x 512 request on a resident slicemap."""
+    import oracle
+    oracle.build()
+    mx, my, mz = sm.dims[0]
+    tx, ty = sm.tiles[0]
+    level = sm.atlases[0].view(ty, my, tx, mx).permute(0, 2, 1, 3).reshape(ty * tx, my, mx)[:mz].cpu().numpy()
+    rng = np.random.default_rng(0)
+    pix = rng.integers(0, 512 * 512, size=32768)
+    t0 = time.perf_counter()
+    ref = oracle.render(level, 8, sm.src_dims, lut.cpu().numpy(), 40.0, 20.0, 512, 512, 0.5, 0.99, 0.0, pixels=pix)
+    dt = time.perf_counter() - t0
+    ns = float(ref["nsamp"][:, 1].sum())
+    return dict(value=ns / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"oracle (C, 1 thread) render of 32768 random rays of a 512x512 view of slicemap 0 "
+                       f"({int(ns)} samples, {dt:.1f} s)")
 
 
 def run_serve(args, wl):
@@ -977,7 +1026,12 @@ def run_serve(args, wl):
         latency_ms=dict(p50=b["p50_ms"], p99=b["p99_ms"]),
         per_view_latency_ms=dict(p50=p["p50_ms"], p99=p["p99_ms"]),
         serving=results,
-        roofline=None,
+        roofline=dict(bound="alu", achieved=FP32_FLOPS_PER_SAMPLE * b["samples_per_s"] / 1e12,
+                      peak=152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12, unit="TFLOP/s",
+                      frac=FP32_FLOPS_PER_SAMPLE * b["samples_per_s"] / 1e12 / (152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12),
+                      kernel="render_batch_kernel", traffic=None,
+                      note="samples/s over the wall time of the top rate, so idle gaps count against it"),
+        cpu_baseline=serve_oracle_baseline(sms[0], luts[0]),
         gpu_launches=None,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
         e2e=e2e,
