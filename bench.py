@@ -37,6 +37,7 @@ before and after container removal.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -112,7 +113,7 @@ def workload(name: str):
 
 
 KERNEL_SOURCES = {"histogram": ["hist.cu"], "slicemap": ["slicemap.cu", "slicemap_common.cuh"],
-                  "render": ["render.cu", "render_common.cuh"], "threshold": ["threshold.cu"]}
+                  "render": ["render_batch.cu", "render_common.cuh"], "threshold": ["threshold.cu"]}
 
 
 def source_sha256(files) -> str:
@@ -192,13 +193,15 @@ class ClockSampler:
                     reasons=reasons, samples=len(rows))
 
 
-def launches_per_step(wl, nviews):
+def launches_per_step(wl, nviews, ntex):
     """Kernels of this library launched by one step: histogram, threshold
     selection, the level-0 slicemap kernel (levels 1-2 fused), one 2x2x2 kernel
-    per further level, one max-grid kernel per level, one render launch per 64
-    views, one image-histogram launch per 1024 views and the entropy kernel."""
+    per further level, one max-grid kernel per level, one texture update per
+    textured level, the work-queue renderer (set-up kernel, one view-upload
+    kernel per 128 views, the render kernel), one image-histogram launch per
+    1024 views, the entropy and best-view kernels."""
     nl = wl["nlevels"]
-    return 1 + 1 + 1 + max(0, nl - 3) + nl + (nviews + 63) // 64 + (nviews + 1023) // 1024 + 1
+    return (1 + 1 + 1 + max(0, nl - 3) + nl + ntex + 2 + (nviews + 127) // 128 + (nviews + 1023) // 1024 + 2)
 
 
 def dist_setup():
@@ -322,7 +325,7 @@ def run_gpu(args, wl):
     stream = torch.cuda.Stream(dev)
     pipe = pl.PreviewPipeline(cfg, dtype, dev, stream)
 
-    stages = ["histogram", "threshold", "slicemap", "render", "entropy"]
+    stages = ["histogram", "threshold", "slicemap", "texture", "render", "entropy"]
     ev = {}
 
     def timer(name):
@@ -334,7 +337,21 @@ def run_gpu(args, wl):
         for _ in range(args.warmup):
             pipe.run(vol, lut)
     torch.cuda.synchronize(dev)
+    if args.render_tuning:
+        w, c, k = (int(x) for x in args.render_tuning.split(","))
+        tuning = pipe.tuning = mctp.BatchTuning(w, c, k)
+    else:
+        tuning, _ = pl.autotune(pipe, lut)
+    with torch.cuda.stream(stream):
+        pipe.run(vol, lut)
+    torch.cuda.synchronize(dev)
     samples_per_step = int(pipe.samples.item())
+    # samples one step evaluates (the rest are skipped as empty): one counted render, untimed
+    mctp.render_batch([pipe.sm], views, pipe._vsm, pipe._vlut, lut, 0.99,
+                      dataclasses.replace(tuning, count_evaluated=True), pipe.images, pipe.samples, pipe.workspace,
+                      stream)
+    evaluated_per_step = mctp.batch_samples_evaluated(pipe.workspace)
+    assert int(pipe.samples.item()) == samples_per_step
 
     clocks = ClockSampler(local)
     if ws > 1:
@@ -400,11 +417,15 @@ def run_gpu(args, wl):
     atlas_bytes = sum(a.numel() * a.element_size() for a in pipe.sm.atlases)
     level0_bytes = pipe.sm.atlases[0].numel() * pipe.sm.atlases[0].element_size()
     image_bytes = pipe.images.numel() * 4
+    # atlas textures: each rendered level's atlas read once and written once into its texture
+    tex_bytes = sum(a.numel() * a.element_size() for a, t in zip(pipe.sm.atlases, pipe.sm.textures or [])
+                    if t is not None)
     sm_mhz = clk.get("sm_mhz") or pk["sm_max_mhz"]
     kernels = {
         "histogram": dict(bound="hbm", bytes=vol_bytes, unit="GB/s"),
         "slicemap": dict(bound="hbm", bytes=vol_bytes + atlas_bytes, unit="GB/s"),
-        "render": dict(bound="alu", flops=FP32_FLOPS_PER_SAMPLE * samples_per_step, unit="TFLOP/s"),
+        "texture": dict(bound="hbm", bytes=2 * tex_bytes, unit="GB/s"),
+        "render": dict(bound="alu", flops=FP32_FLOPS_PER_SAMPLE * evaluated_per_step, unit="TFLOP/s"),
         "threshold": dict(bound="alu", flops=0, unit="TFLOP/s"),
         "entropy": dict(bound="hbm", bytes=image_bytes, unit="GB/s"),
     }
@@ -434,8 +455,10 @@ def run_gpu(args, wl):
                        entropy_bits=float(pipe.entropy[best_view].item())),
         config=dict(workload=wl["desc"], l2="inputs larger than L2 (14.6 GB volume; no flush)"
                     if vol_bytes > 200e6 else "input fits in L2 (L2-resident numbers)",
-                    parallelism=f"replicas x{ws}"),
+                    parallelism=f"replicas x{ws}", renderer="render_batch (work queue)",
+                    tuning=dict(warp_w=tuning.warp_w, chunk=tuning.chunk, ctas_per_sm=tuning.ctas_per_sm)),
         samples_per_step=samples_per_step,
+        samples_evaluated_per_step=evaluated_per_step,
         slicemap_gbs=roof["slicemap"]["achieved"], slicemap_frac_of_hbm_peak=roof["slicemap"]["frac"],
         histogram_gbs=roof["histogram"]["achieved"],
         render_samples_per_s=samples_per_step / (stage_ms["render"] / 1e3),
@@ -443,7 +466,8 @@ def run_gpu(args, wl):
         stage_ms=stage_ms,
         roofline=dict(roof[dominant], kernel=dominant, peak_source=pk["source"]),
         roofline_by_kernel=roof,
-        gpu_launches=launches_per_step(wl, len(views)) * args.steps,
+        gpu_launches=launches_per_step(wl, len(views), sum(t is not None for t in pipe.sm.textures or []))
+        * args.steps,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
         e2e=dict(value=samples_per_step / e2e_s, unit=UNIT, h2d_bytes_per_step=vol_bytes,
                  d2h_bytes_per_step=image_bytes, ms_per_step=e2e_s * 1e3),
@@ -536,6 +560,11 @@ def run_batch(args, wl):
 
     t_batched = timed(batched, 3)
     samples_per_step = int(pipe.samples.item())
+    with torch.cuda.stream(stream):
+        mctp.render_batch(pipe.slicemaps, pipe.views, pipe.view_slicemap, pipe.view_lut, pipe.luts, 0.99,
+                          dataclasses.replace(pipe.tuning, count_evaluated=True), pipe.images, pipe.samples,
+                          pipe.workspace, stream)
+    evaluated_per_step = mctp.batch_samples_evaluated(pipe.workspace)
     ref_images = pipe.images.clone()
     t_per_volume = timed(per_volume, 3)
     torch.cuda.synchronize(dev)
@@ -630,7 +659,7 @@ def run_batch(args, wl):
     atlas_bytes = sum(sm.nbytes for sm in pipe.slicemaps)
     prep_bytes = 2 * vol_bytes + atlas_bytes   # histogram read + slicemap read + atlas writes
     render_s = stage_ms["render"] / 1e3
-    ach = FP32_FLOPS_PER_SAMPLE * samples_per_step / render_s / 1e12
+    ach = FP32_FLOPS_PER_SAMPLE * evaluated_per_step / render_s / 1e12
     roof = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak, kernel="render",
                 ms=stage_ms["render"], traffic=None, peak_source="FP32 issue rate at the maximum SM clock")
     value = samples_per_step * args.steps * ws / elapsed
@@ -641,7 +670,7 @@ def run_batch(args, wl):
         config=dict(workload=wl["desc"], l2="inputs larger than L2 (%.1f GB of volumes; no flush)" % (vol_bytes / 1e9),
                     parallelism=f"replicas x{ws}", tuning=dict(warp_w=best.warp_w, chunk=best.chunk,
                                                                ctas_per_sm=best.ctas_per_sm)),
-        samples_per_step=samples_per_step,
+        samples_per_step=samples_per_step, samples_evaluated_per_step=evaluated_per_step,
         stage_ms=stage_ms,
         prepare_gbs=prep_bytes / (stage_ms["prepare"] / 1e3) / 1e9,
         prepare_frac_of_hbm_peak=prep_bytes / (stage_ms["prepare"] / 1e3) / 1e9 / pk["hbm_gbs"],
@@ -958,6 +987,8 @@ def run_serve(args, wl):
         keep, _ = mctp.select_threshold(h, 256)
         sm = mctp.Slicemap.allocate((sp.nx, sp.ny, sp.nz), wl["level0"], wl["nlevels"], torch.uint8, 8, dev)
         mctp.build_slicemap(v, 8, sm, keep)
+        sm.make_textures()  # the batched server gathers corner quads through atlas textures
+        sm.update_textures()
         vols.append(v)
         sms.append(sm)
     luts = torch.from_numpy(np.stack(phantom.preset_luts())).to(dev)
@@ -1016,6 +1047,15 @@ def run_serve(args, wl):
     top = wl["rates"][-1]
     b, p = results["batched"][top], results["per_view"][top]
     pk = peaks()
+    # share of taken samples that are evaluated (not skipped as empty), from one counted
+    # batch of the top rate's first 256 requests
+    probe = sv.poisson_trace(top, 256, len(sms), luts.shape[0], seed=len(wl["rates"]))
+    pv = [a.view for a in probe]
+    pvs = [a.slicemap for a in probe]
+    pvl = [a.lut for a in probe]
+    _, psamp, pws = mctp.render_batch(sms, pv, pvs, pvl, luts, 0.99, mctp.BatchTuning(count_evaluated=True))
+    eval_share = mctp.batch_samples_evaluated(pws) / max(int(psamp.item()), 1)
+    del pws
     line = dict(
         metric=METRIC, value=b["samples_per_s"] * ws, unit=UNIT, n_gpus=ws, steps=len(wl["rates"]),
         warmup=1, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u8/f32",
@@ -1026,11 +1066,13 @@ def run_serve(args, wl):
         latency_ms=dict(p50=b["p50_ms"], p99=b["p99_ms"]),
         per_view_latency_ms=dict(p50=p["p50_ms"], p99=p["p99_ms"]),
         serving=results,
-        roofline=dict(bound="alu", achieved=FP32_FLOPS_PER_SAMPLE * b["samples_per_s"] / 1e12,
+        roofline=dict(bound="alu", achieved=FP32_FLOPS_PER_SAMPLE * eval_share * b["samples_per_s"] / 1e12,
                       peak=152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12, unit="TFLOP/s",
-                      frac=FP32_FLOPS_PER_SAMPLE * b["samples_per_s"] / 1e12 / (152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12),
-                      kernel="render_batch_kernel", traffic=None,
-                      note="samples/s over the wall time of the top rate, so idle gaps count against it"),
+                      frac=FP32_FLOPS_PER_SAMPLE * eval_share * b["samples_per_s"] / 1e12
+                      / (152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12),
+                      kernel="render_batch_kernel", traffic=None, evaluated_share=eval_share,
+                      note="evaluated samples/s over the wall time of the top rate, so idle gaps count against it; "
+                           "the evaluated share is from one counted batch of 256 requests of that rate"),
         cpu_baseline=serve_oracle_baseline(sms[0], luts[0]),
         gpu_launches=None,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
@@ -1053,6 +1095,8 @@ def main():
     ap.add_argument("--workload", default="full",
                     choices=["full", "mid", "slab", "small", "batch", "serve", "fit", "thresholds"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--render-tuning", default=None, metavar="WARP_W,CHUNK,CTAS",
+                    help="fixed launch shape of the work-queue renderer (default: autotuned after warm-up)")
     args = ap.parse_args()
     wl = workload(args.workload)
     if args.impl == "reference":

@@ -95,6 +95,7 @@ typedef struct {
     int32_t tiles_y[MCTP_MAX_LEVELS];
     void *atlas[MCTP_MAX_LEVELS];     /* device, (tiles_y*my) x (tiles_x*mx) elements each */
     void *maxgrid[MCTP_MAX_LEVELS];   /* device or NULL: per-cell maxima of the level (below) */
+    uint64_t texture[MCTP_MAX_LEVELS];/* 0 or the handle of an atlas texture of level k (below) */
 } mctp_slicemap;
 
 /* Occupancy data of a level (an acceleration structure of this library; the
@@ -106,6 +107,34 @@ typedef struct {
  * can reach a transfer-function opacity above zero.  Skipped samples have
  * opacity exactly zero, so images and sample counts are unchanged. */
 #define MCTP_MAXGRID_CELL 8
+
+/*
+ * Atlas textures (an option of this library's renderers).  The paper's
+ * client samples each atlas as a 2D texture (Sec. III-B/C); here a level's
+ * atlas can be copied into a 2D CUDA array with a texture object, and when
+ * sm->texture[k] holds its handle, mctp_render_batch (and the server) fetch
+ * a sample's four in-slice corners with one texture gather per slice instead
+ * of four loads.  The gathered values are the atlas values, so images and
+ * sample counts are bit-identical with and without a texture.
+ *   mctp_atlas_texture_create  allocates the array for level `level` of *sm
+ *       ((tiles_y*my) x (tiles_x*mx) elements of its dtype) and its texture
+ *       object; *out owns both, *handle receives the value for
+ *       sm->texture[level].  The contents are undefined until an update.
+ *   mctp_atlas_texture_update  copies atlas[level] into the array (device to
+ *       device, on `stream`); call it after every mctp_build_slicemap of
+ *       that slicemap, before rendering.  The slicemap must have the same
+ *       level geometry and dtype as at creation.
+ *   mctp_atlas_texture_destroy frees both (NULL is allowed); the caller
+ *       makes sure no launch that uses the handle is still running.
+ * Errors: MCTP_EINVAL (null pointers, bad slicemap or level, geometry
+ *         differing from creation), MCTP_ESIZE (atlas wider or taller than
+ *         the device's texture-gather limit, 32768 on this part),
+ *         MCTP_ECUDA (allocation or copy failed).
+ */
+typedef struct mctp_atlas_texture mctp_atlas_texture;
+int mctp_atlas_texture_create(const mctp_slicemap *sm, int32_t level, mctp_atlas_texture **out, uint64_t *handle);
+int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slicemap *sm, int32_t level, void *stream);
+int mctp_atlas_texture_destroy(mctp_atlas_texture *t);
 
 /* One orthographic view of a slicemap level.  The camera looks at the centre
  * of the source box from azimuth az (about +z, from +x) and elevation el;
@@ -242,7 +271,13 @@ int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views, int32_t n
  *                 mctp_render_batch_workspace gives for the same arguments,
  *                 256-byte aligned, owned by the caller; its contents need no
  *                 initialisation and are rewritten by every call, so two
- *                 calls in flight at once must not share it
+ *                 calls in flight at once must not share it.  When the call
+ *                 has run with MCTP_BATCH_COUNT_EVALUATED, bytes 8..15 of the
+ *                 workspace hold (uint64) the number of samples evaluated:
+ *                 the samples taken minus those skipped as empty, i.e. the
+ *                 samples whose corners were fetched and looked up.
+ * When every (slicemap, level) of the batch has an atlas texture
+ * (sm->texture[level] != 0), corner quads are gathered through the textures.
  * Everything is enqueued on `stream` (kernel launches and memsets only; no
  * host synchronisation), so a call can be captured in a CUDA graph.
  * Errors: MCTP_EINVAL (null pointers, an index out of range, bad view,
@@ -256,8 +291,12 @@ typedef struct {
                             warp_w x 32/warp_w pixels); 0 = 8 */
     int32_t chunk;       /* warp tiles taken per queue access, 1..64; 0 = 2 */
     int32_t ctas_per_sm; /* cap on resident CTAs per SM; 0 = occupancy limit */
-    int32_t reserved;    /* must be 0 */
+    int32_t flags;       /* 0 or MCTP_BATCH_COUNT_EVALUATED */
 } mctp_batch_tuning;
+
+/* count the evaluated samples into bytes 8..15 of the workspace (a register
+ * more in the march, so a little slower); without it those bytes are 0 */
+#define MCTP_BATCH_COUNT_EVALUATED 1
 
 int mctp_render_batch_workspace(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
                                 const int32_t *view_slicemap, const int32_t *view_lut, int32_t nviews,

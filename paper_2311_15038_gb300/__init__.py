@@ -19,8 +19,9 @@ from . import _lib
 from ._lib import MctpError  # noqa: F401
 
 __all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
-           "render_batch", "render_batch_workspace", "render_batch_static", "BatchTuning", "image_entropy",
-           "find_container", "mask_container", "Slicemap", "View", "default_tiles",
+           "render_batch", "render_batch_workspace", "render_batch_static", "batch_samples_evaluated", "BatchTuning",
+           "image_entropy",
+           "find_container", "mask_container", "Slicemap", "AtlasTexture", "View", "default_tiles",
            "atlas_bytes", "version", "MctpError"]
 
 _DTYPES = {torch.uint8: (_lib.MCTP_U8, 1), torch.uint16: (_lib.MCTP_U16, 2), torch.int16: (_lib.MCTP_U16, 2)}
@@ -123,6 +124,7 @@ class Slicemap:
     bits: int
     dtype: torch.dtype
     maxgrids: list[torch.Tensor] | None = None
+    textures: list["AtlasTexture | None"] | None = None  # per level; see make_textures
 
     @classmethod
     def allocate(cls, src_dims, level0_dims, nlevels: int, dtype: torch.dtype, bits: int, device="cuda",
@@ -156,15 +158,71 @@ class Slicemap:
             s.atlas[k] = at.data_ptr()
             if self.maxgrids is not None and self.maxgrids[k] is not None:
                 s.maxgrid[k] = _cuda(self.maxgrids[k], "maxgrid").data_ptr()
+            if self.textures is not None and self.textures[k] is not None:
+                s.texture[k] = self.textures[k].handle
         return s
+
+    def make_textures(self, levels=None) -> "Slicemap":
+        """Give the listed levels (default: all) an atlas texture; the batched
+        renderer then gathers corner quads through it.  Call update_textures
+        after every build_slicemap."""
+        levels = range(len(self.dims)) if levels is None else levels
+        if self.textures is None:
+            self.textures = [None] * len(self.dims)
+        for k in levels:
+            if self.textures[k] is None:
+                self.textures[k] = AtlasTexture(self, k)
+        return self
+
+    def update_textures(self, stream=None) -> None:
+        """Copy the atlases into their textures (device to device, on stream)."""
+        for t in self.textures or []:
+            if t is not None:
+                t.update(self, stream)
 
     def without_maxgrid(self) -> "Slicemap":
         """The same atlases with no occupancy data (renders evaluate every sample)."""
-        return Slicemap(self.src_dims, self.dims, self.tiles, self.atlases, self.bits, self.dtype, None)
+        return Slicemap(self.src_dims, self.dims, self.tiles, self.atlases, self.bits, self.dtype, None,
+                        self.textures)
+
+    def without_textures(self) -> "Slicemap":
+        """The same atlases and max grids, rendered with loads from the atlases."""
+        return Slicemap(self.src_dims, self.dims, self.tiles, self.atlases, self.bits, self.dtype, self.maxgrids)
 
     @property
     def nbytes(self) -> int:
         return sum(a.numel() * a.element_size() for a in self.atlases)
+
+
+class AtlasTexture:
+    """Level `level` of a slicemap's atlas as a 2D texture (mctp_atlas_texture_*),
+    owning a CUDA array of the atlas's size; freed by close() or when collected."""
+
+    def __init__(self, sm: "Slicemap", level: int):
+        self.level = level
+        self._ptr = ctypes.c_void_p()
+        h = ctypes.c_uint64()
+        d = sm.desc()
+        _lib.check(_lib.load().mctp_atlas_texture_create(ctypes.byref(d), level, ctypes.byref(self._ptr),
+                                                          ctypes.byref(h)), "mctp_atlas_texture_create")
+        self.handle = h.value
+
+    def update(self, sm: "Slicemap", stream=None) -> None:
+        d = sm.desc()
+        _lib.check(_lib.load().mctp_atlas_texture_update(self._ptr, ctypes.byref(d), self.level, _stream(stream)),
+                   "mctp_atlas_texture_update")
+
+    def close(self) -> None:
+        if self._ptr:
+            _lib.check(_lib.load().mctp_atlas_texture_destroy(self._ptr), "mctp_atlas_texture_destroy")
+            self._ptr = ctypes.c_void_p()
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def build_slicemap(vol: torch.Tensor, bits: int, sm: Slicemap, keep: torch.Tensor | None = None,
@@ -232,9 +290,11 @@ class BatchTuning:
     warp_w: int = 8       # a warp covers warp_w x 32/warp_w pixels (4, 8, 16 or 32)
     chunk: int = 2        # warp tiles taken per queue access (1..64)
     ctas_per_sm: int = 0  # cap on resident CTAs per SM (0 = occupancy limit)
+    count_evaluated: bool = False  # count evaluated samples (batch_samples_evaluated); a little slower
 
     def c(self) -> _lib.BatchTuning:
-        return _lib.BatchTuning(self.warp_w, self.chunk, self.ctas_per_sm, 0)
+        return _lib.BatchTuning(self.warp_w, self.chunk, self.ctas_per_sm,
+                                _lib.MCTP_BATCH_COUNT_EVALUATED if self.count_evaluated else 0)
 
 
 class _BatchArgs:
@@ -299,6 +359,14 @@ def render_batch(slicemaps, views, view_slicemap, view_lut, luts: torch.Tensor, 
                                      luts.shape[1], alpha_stop, ctypes.byref(t), _ptr(out), _ptr(samples),
                                      _ptr(workspace), workspace.numel(), _stream(stream)), "mctp_render_batch")
     return out, samples, workspace
+
+
+def batch_samples_evaluated(workspace: torch.Tensor) -> int:
+    """Samples the last render_batch call on this workspace evaluated (taken
+    minus those skipped as empty) when it ran with count_evaluated, else 0;
+    waits for all work on the workspace's device first."""
+    torch.cuda.synchronize(workspace.device)
+    return int(workspace[8:16].view(torch.int64).item())
 
 
 def render_batch_static(slicemaps, views, view_slicemap, view_lut, luts: torch.Tensor, alpha_stop: float = 0.99,

@@ -10,6 +10,7 @@ MCTP_OK = 0
 MCTP_EINVAL = -1
 MCTP_EUNSUPPORTED = -2
 MCTP_ESIZE = -3
+MCTP_BATCH_COUNT_EVALUATED = 1
 MCTP_ECUDA = -4
 
 MCTP_U8 = 1
@@ -44,7 +45,8 @@ class SlicemapDesc(ctypes.Structure):
     _fields_ = [("nlevels", C_I32), ("dtype", C_I32), ("bits", C_I32), ("reserved", C_I32),
                 ("src_dims", C_I64 * 3), ("dims", (C_I32 * 3) * MCTP_MAX_LEVELS),
                 ("tiles_x", C_I32 * MCTP_MAX_LEVELS), ("tiles_y", C_I32 * MCTP_MAX_LEVELS),
-                ("atlas", C_VP * MCTP_MAX_LEVELS), ("maxgrid", C_VP * MCTP_MAX_LEVELS)]
+                ("atlas", C_VP * MCTP_MAX_LEVELS), ("maxgrid", C_VP * MCTP_MAX_LEVELS),
+                ("texture", ctypes.c_uint64 * MCTP_MAX_LEVELS)]
 
 
 class ViewDesc(ctypes.Structure):
@@ -53,7 +55,7 @@ class ViewDesc(ctypes.Structure):
 
 
 class BatchTuning(ctypes.Structure):
-    _fields_ = [("warp_w", C_I32), ("chunk", C_I32), ("ctas_per_sm", C_I32), ("reserved", C_I32)]
+    _fields_ = [("warp_w", C_I32), ("chunk", C_I32), ("ctas_per_sm", C_I32), ("flags", C_I32)]
 
 
 class ServeParams(ctypes.Structure):
@@ -101,6 +103,10 @@ EXPORTS = {
     "mctp_l2_loss": ([C_VP, C_VP, C_I64, ctypes.c_float, C_VP, C_VP, C_VP], ctypes.c_int),
     "mctp_adam_step": ([C_VP, C_VP, C_VP, C_VP, C_I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                         ctypes.c_float, C_I32, ctypes.c_float, ctypes.c_float, C_VP], ctypes.c_int),
+    "mctp_atlas_texture_create": ([ctypes.POINTER(SlicemapDesc), C_I32, ctypes.POINTER(C_VP),
+                                   ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "mctp_atlas_texture_update": ([C_VP, ctypes.POINTER(SlicemapDesc), C_I32, C_VP], ctypes.c_int),
+    "mctp_atlas_texture_destroy": ([C_VP], ctypes.c_int),
     "mctp_image_entropy": ([C_VP, ctypes.POINTER(ViewDesc), C_I32, C_VP, C_VP, C_VP, C_VP], ctypes.c_int),
     "mctp_container_workspace": ([C_I64, C_I64], ctypes.c_size_t),
     "mctp_find_container": ([C_VP, ctypes.POINTER(VolumeDesc), C_I64, C_I64, C_I32, C_I32, C_I32, C_VP, C_VP, C_VP,

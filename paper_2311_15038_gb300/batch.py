@@ -13,8 +13,9 @@ from dataclasses import asdict, dataclass
 
 import torch
 
-from . import (BatchTuning, Slicemap, View, build_histogram, build_slicemap, render_batch, render_batch_workspace,
-               select_threshold)
+from . import (BatchTuning, Slicemap, View, _lib, build_histogram, build_slicemap, render_batch,
+               render_batch_workspace, select_threshold)
+from ._lib import MctpError
 
 WARP_WIDTHS = (4, 8, 16, 32)
 CHUNKS = (1, 2, 4, 8, 16)
@@ -85,8 +86,10 @@ def _signature(slicemaps, views, view_slicemap, luts) -> str:
     dims = sorted({(sm.dims[v.level], str(sm.dtype)) for v, s in zip(views, view_slicemap)
                    for sm in [slicemaps[s]]})
     pix = sum(v.width * v.height for v in views)
+    gather = all(sm.textures is not None and sm.textures[v.level] is not None
+                 for v, s in zip(views, view_slicemap) for sm in [slicemaps[s]])
     return json.dumps(dict(levels=[list(d) + [t] for d, t in dims][:16], nviews=len(views), pixels=pix,
-                           nlut=int(luts.shape[-2])))
+                           nlut=int(luts.shape[-2]), gather=gather))
 
 
 @dataclass
@@ -103,7 +106,7 @@ class BatchPipeline:
 
     def __init__(self, items: list[BatchItem], level0, nlevels: int, luts: torch.Tensor, nbins: int = 256,
                  mode: str = "otsu", alpha_stop: float = 0.99, tuning: BatchTuning | None = None,
-                 device="cuda", stream=None, maxgrid: bool = True):
+                 device="cuda", stream=None, maxgrid: bool = True, texture: bool = True):
         self.items = items
         self.device = torch.device(device)
         self.stream = stream or torch.cuda.current_stream(self.device)
@@ -126,6 +129,16 @@ class BatchPipeline:
                 self.views.append(v)
                 self.view_slicemap.append(i)
                 self.view_lut.append(it.lut)
+        if texture:
+            # atlas textures of the rendered levels; the render gathers corner quads through them
+            # when every (slicemap, level) has one, else it loads from the atlases
+            for i, it in enumerate(items):
+                for k in sorted({v.level for v in it.views}):
+                    try:
+                        self.slicemaps[i].make_textures([k])
+                    except MctpError as e:
+                        if e.code != _lib.MCTP_ESIZE:
+                            raise
         total = sum(v.width * v.height * 4 for v in self.views)
         self.images = torch.empty(max(total, 4), dtype=torch.float32, device=self.device)
         self.samples = torch.empty(1, dtype=torch.uint64, device=self.device)
@@ -144,6 +157,7 @@ class BatchPipeline:
                              stream=s)
             keep = self.keep[i]
         build_slicemap(it.volume, it.bits, self.slicemaps[i], keep, s)
+        self.slicemaps[i].update_textures(s)
 
     def render(self):
         render_batch(self.slicemaps, self.views, self.view_slicemap, self.view_lut, self.luts, self.alpha_stop,

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
     const int skip_S = sh_skip;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long taken_total = 0;
+    uint32_t taken = 0, evaluated = 0;  // the evaluated count is not reported by this renderer
     int v = 0, cur_level = -1;
     bool use_skip = false;
     LevelGeom G{};
@@ -103,15 +103,12 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
         const int py = int(t / V.tiles_w) * kTileH + (warp >> 1) * 4 + (lane >> 3);
         if (px >= V.W || py >= V.H) continue;
         const float4 acc = march_ray<T>(V, static_cast<const T *>(Lv.atlas), G, use_skip, tab, P.nlut,
-                                        P.inv_vmax, P.alpha_stop, px, py, taken_total);
+                                        P.inv_vmax, P.alpha_stop, px, py, taken, evaluated);
         reinterpret_cast<float4 *>(P.out + V.out_offset)[int64_t(py) * V.W + px] = acc;
+        flush_count(taken, P.samples);
+        evaluated = 0;
     }
-    if (P.samples) {
-        unsigned long long t = taken_total;
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o2);
-        if (lane == 0 && t) atomicAdd(P.samples, t);
-    }
+    warp_add_count(taken, P.samples);
 }
 
 }  // namespace

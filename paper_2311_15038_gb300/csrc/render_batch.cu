@@ -41,6 +41,7 @@ constexpr size_t kAlign = 256;
 // One (slicemap, level, transfer function) combination used by the batch.
 struct BatchPair {
     const void *atlas;
+    uint64_t tex;             // atlas texture (0: loads from the atlas)
     const uint16_t *maxgrid;  // nullptr: no skipping
     uint32_t *slice_off;      // workspace: atlas offset of each slice
     uint32_t *occ;            // workspace: cell bitmap (when maxgrid is set)
@@ -87,6 +88,7 @@ struct BatchArgs {
     float *out;
     unsigned long long *samples;
     unsigned int *counter;
+    unsigned long long *counter_evaluated;  // workspace bytes 8..15
     int32_t nviews, nlut, nluts;
     uint32_t total_items;
     int32_t wx_log2;  // log2 warp_w
@@ -97,6 +99,7 @@ struct BatchArgs {
 __global__ void __launch_bounds__(kBatchThreads) batch_upload_kernel(const __grid_constant__ UploadArgs A)
 {
     static_assert(sizeof(BatchView) % 4 == 0, "word copy");
+    static_assert(sizeof(PrepArgs) <= 32000, "kernel parameter space");
     const uint32_t *src = reinterpret_cast<const uint32_t *>(A.view);
     uint32_t *dst = reinterpret_cast<uint32_t *>(A.dst + A.first);
     const int nw = A.count * int(sizeof(BatchView) / 4);
@@ -129,7 +132,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_prep_kernel(const __grid_
     const int z1 = min(p.mz, (part + 1) * zper);
     for (int z = part * zper + threadIdx.x; z < z1; z += blockDim.x) {
         const int row = z / p.tiles_x, col = z - row * p.tiles_x;
-        p.slice_off[z] = uint32_t(int64_t(row) * p.my * p.pitch + int64_t(col) * p.mx);
+        p.slice_off[z] = p.tex ? uint32_t(col * p.mx) | (uint32_t(row * p.my) << 16)
+                               : uint32_t(int64_t(row) * p.my * p.pitch + int64_t(col) * p.mx);
     }
     if (use_skip) {
         const int nwords = p.gy * p.gz * p.wpr;
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_prep_kernel(const __grid_
     }
 }
 
-template <typename T, bool kLutShared>
+template <typename T, bool kLutShared, bool kGather, bool kCount>
 __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __grid_constant__ BatchArgs P)
 {
     extern __shared__ __align__(16) float4 slut[];
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __
     const int gxl = wxl >= 4 ? 0 : 4 - wxl, gyl = 3 - gxl;
     const int lx = lane & ((1 << wxl) - 1), ly = lane >> wxl;
 
-    unsigned long long taken = 0;
+    uint32_t taken = 0, evaluated = 0;
     int v = -1;
     uint32_t vbegin = 0, vend = 0;
     const uint32_t chunk = uint32_t(P.chunk);
@@ -193,22 +197,41 @@ __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __
             const BatchPair &PR = P.pairs[BV.pair];
             const LevelGeom G{{PR.mx - 1, PR.my - 1, PR.mz - 1}, uint32_t(PR.pitch), PR.gy, PR.wpr};
             const float4 *lut = (kLutShared ? slut : P.luts) + int64_t(PR.lut) * P.nlut;
-            const CachedTables<kLutShared> tab{lut, PR.slice_off, PR.occ};
-            const float4 acc = march_ray<T>(BV.vp, static_cast<const T *>(PR.atlas), G, PR.use_skip != 0, tab,
-                                            P.nlut, PR.inv_vmax, P.alpha_stop, px, py, taken);
+            float4 acc;
+            if constexpr (kGather) {
+                const GatherTables<kLutShared> tab{lut, PR.slice_off, PR.occ, cudaTextureObject_t(PR.tex)};
+                acc = march_ray<T, kCount>(BV.vp, static_cast<const T *>(PR.atlas), G, PR.use_skip != 0, tab, P.nlut,
+                                   PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated);
+            } else {
+                const CachedTables<kLutShared> tab{lut, PR.slice_off, PR.occ};
+                acc = march_ray<T, kCount>(BV.vp, static_cast<const T *>(PR.atlas), G, PR.use_skip != 0, tab, P.nlut,
+                                   PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated);
+            }
             reinterpret_cast<float4 *>(P.out + BV.vp.out_offset)[int64_t(py) * BV.vp.W + px] = acc;
+            flush_count(taken, P.samples);
+            if (kCount) flush_count(evaluated, P.counter_evaluated);
         }
     }
-    if (P.samples) {
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) taken += __shfl_xor_sync(0xffffffffu, taken, o2);
-        if (lane == 0 && taken) atomicAdd(P.samples, taken);
-    }
+    warp_add_count(taken, P.samples);
+    if (kCount) warp_add_count(evaluated, P.counter_evaluated);
+}
+
+template <typename T>
+auto pick_kernel(bool lut_shared, bool gather, bool count) -> void (*)(BatchArgs)
+{
+    if (gather)
+        return lut_shared ? (count ? render_batch_kernel<T, true, true, true> : render_batch_kernel<T, true, true, false>)
+                          : (count ? render_batch_kernel<T, false, true, true>
+                                   : render_batch_kernel<T, false, true, false>);
+    return lut_shared ? (count ? render_batch_kernel<T, true, false, true> : render_batch_kernel<T, true, false, false>)
+                      : (count ? render_batch_kernel<T, false, false, true>
+                               : render_batch_kernel<T, false, false, false>);
 }
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Workspace layout of a batch: the queue counter, view records, the queue
+// Workspace layout of a batch: the queue counter (bytes 0..3) and the count of
+// evaluated samples (bytes 8..15) in the first 256 bytes, view records, the queue
 // start of each view, pair records, then per pair its slice offsets and cell
 // bitmap.
 struct Plan {
@@ -308,7 +331,8 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
         if (tun.chunk == 0) tun.chunk = 2;
     }
     const int wxl = log2_exact(tun.warp_w);
-    if (wxl < 2 || wxl > 5 || tun.chunk < 1 || tun.chunk > 64 || tun.ctas_per_sm < 0 || tun.reserved != 0)
+    if (wxl < 2 || wxl > 5 || tun.chunk < 1 || tun.chunk > 64 || tun.ctas_per_sm < 0 ||
+        (tun.flags & ~MCTP_BATCH_COUNT_EVALUATED) != 0)
         return MCTP_EINVAL;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1))) return MCTP_EINVAL;
     if (workspace_bytes < plan.total) return MCTP_ESIZE;
@@ -317,12 +341,15 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
         for (int i = 0; i < nviews; ++i)
             if (out_offsets[i] < 0 || (out_offsets[i] & 3)) return MCTP_EINVAL;
     if (samples_taken && cudaMemsetAsync(samples_taken, 0, sizeof(uint64_t), s) != cudaSuccess) return MCTP_ECUDA;
-    if (nviews == 0) return MCTP_OK;
+    if (nviews == 0) return cudaMemsetAsync(workspace, 0, 16, s) == cudaSuccess ? MCTP_OK : MCTP_ECUDA;
     uint8_t *ws = static_cast<uint8_t *>(workspace);
     BatchView *ws_views = reinterpret_cast<BatchView *>(ws + plan.views_at);
     uint32_t *ws_begin = reinterpret_cast<uint32_t *>(ws + plan.begin_at);
     BatchPair *ws_pairs = reinterpret_cast<BatchPair *>(ws + plan.pairs_at);
     const float4 *luts = reinterpret_cast<const float4 *>(luts_rgba);
+    // corners by texture gathers when every (slicemap, level) of the batch has an atlas texture
+    bool gather = !plan.pairs.empty();
+    for (const auto &pr : plan.pairs) gather = gather && sms[std::get<0>(pr)].texture[std::get<1>(pr)] != 0;
 
     // ---- pair records and tables
     {
@@ -342,6 +369,7 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
                 p = BatchPair{};
                 const int c = MCTP_MAXGRID_CELL;
                 p.atlas = sm.atlas[k];
+                p.tex = gather ? sm.texture[k] : 0;
                 p.maxgrid = static_cast<const uint16_t *>(sm.maxgrid[k]);
                 p.slice_off = reinterpret_cast<uint32_t *>(ws + plan.slice_at[size_t(first + i)]);
                 p.occ = reinterpret_cast<uint32_t *>(ws + plan.occ_at[size_t(first + i)]);
@@ -404,7 +432,7 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
     }
 
     // ---- the persistent march over the queue
-    if (cudaMemsetAsync(ws, 0, sizeof(unsigned int), s) != cudaSuccess) return MCTP_ECUDA;
+    if (cudaMemsetAsync(ws, 0, 16, s) != cudaSuccess) return MCTP_ECUDA;  // queue counter, evaluated samples
     BatchArgs P{};
     P.views = ws_views;
     P.item_begin = ws_begin;
@@ -413,6 +441,7 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
     P.out = out_rgba;
     P.samples = reinterpret_cast<unsigned long long *>(samples_taken);
     P.counter = reinterpret_cast<unsigned int *>(ws);
+    P.counter_evaluated = reinterpret_cast<unsigned long long *>(ws + 8);
     P.nviews = nviews;
     P.nlut = nlut;
     P.nluts = nluts;
@@ -423,11 +452,9 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
     const size_t lut_bytes = size_t(nluts) * size_t(nlut) * sizeof(float4);
     const bool lut_shared = lut_bytes <= kLutSmemMax;
     const size_t smem = lut_shared ? lut_bytes : 0;
-    void (*kern)(BatchArgs);
-    if (sms[0].dtype == MCTP_U8)
-        kern = lut_shared ? render_batch_kernel<uint8_t, true> : render_batch_kernel<uint8_t, false>;
-    else
-        kern = lut_shared ? render_batch_kernel<uint16_t, true> : render_batch_kernel<uint16_t, false>;
+    const bool count = (tun.flags & MCTP_BATCH_COUNT_EVALUATED) != 0;
+    void (*kern)(BatchArgs) = sms[0].dtype == MCTP_U8 ? pick_kernel<uint8_t>(lut_shared, gather, count)
+                                                      : pick_kernel<uint16_t>(lut_shared, gather, count);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem) != cudaSuccess)
         return MCTP_ECUDA;

@@ -149,6 +149,7 @@ __device__ __forceinline__ uint32_t occupancy_word(const uint16_t *maxgrid, int 
 // slice and the cell bitmap, from shared memory or through the read-only
 // cache.
 struct SharedTables {
+    static constexpr bool kGather = false;
     const float4 *lut;
     const uint32_t *slice_off;
     const uint32_t *occ;
@@ -159,6 +160,7 @@ struct SharedTables {
 
 template <bool kLutShared>
 struct CachedTables {
+    static constexpr bool kGather = false;
     const float4 *lut;
     const uint32_t *slice_off;
     const uint32_t *occ;
@@ -167,12 +169,52 @@ struct CachedTables {
     __device__ __forceinline__ uint32_t occ_at(int w) const { return __ldg(occ + w); }
 };
 
+// Atlas texture of the level (mctp_atlas_texture_*): slice_at(z) is then the
+// texel origin of slice z's tile, x | y << 16, and the four in-slice corners
+// of a sample come from one gather.
+template <bool kLutShared>
+struct GatherTables {
+    static constexpr bool kGather = true;
+    const float4 *lut;
+    const uint32_t *slice_off;
+    const uint32_t *occ;
+    cudaTextureObject_t tex;
+    __device__ __forceinline__ float4 lut_at(int j) const { return kLutShared ? lut[j] : __ldg(lut + j); }
+    __device__ __forceinline__ uint32_t slice_at(int z) const { return __ldg(slice_off + z); }
+    __device__ __forceinline__ uint32_t occ_at(int w) const { return __ldg(occ + w); }
+};
+
+template <typename T> struct Quad;
+template <> struct Quad<uint8_t> { using type = uchar4; };
+template <> struct Quad<uint16_t> { using type = ushort4; };
+
+// Corners (x0, y0), (x1, y0), (x0, y1), (x1, y1) of the slice whose tile
+// starts at texel `origin`; x1 is x0 + 1 or, clamped at the level's edge,
+// x0 (likewise y1).  The gather at texel coordinate (X + 1, Y + 1) returns the
+// 2x2 block whose lower corner is (X, Y), in the order (X, Y+1), (X+1, Y+1),
+// (X+1, Y), (X, Y) (the bilinear footprint order of texture gathers).
+template <typename T>
+__device__ __forceinline__ void gather_quad(cudaTextureObject_t tex, uint32_t origin, int x0, int y0, bool dx,
+                                            bool dy, float &v00, float &v10, float &v01, float &v11)
+{
+    const float gx = float(int(origin & 0xffffu) + x0 + 1), gy = float(int(origin >> 16) + y0 + 1);
+    const typename Quad<T>::type g = tex2Dgather<typename Quad<T>::type>(tex, gx, gy, 0);
+    const float a = float(g.w), b = float(g.z), c = float(g.x), d = float(g.y);
+    v00 = a;
+    v10 = dx ? b : a;
+    v01 = dy ? c : a;
+    v11 = dx ? (dy ? d : b) : (dy ? c : a);
+}
+
 // March the ray of pixel (px, py) of view V through a level; returns the
-// premultiplied (C, A) and adds the number of samples taken to `taken`.
-template <typename T, class Tab>
+// premultiplied (C, A), adds the number of samples taken to `taken` and the
+// number of them evaluated (not skipped as empty) to `evaluated` (kCount;
+// the count costs a register in the loop).  Each adds less than 2^31; callers
+// keep their 32-bit sums below 2^31 between rays (flush_count).
+template <typename T, bool kCount = false, class Tab>
 __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas, const LevelGeom &G, bool use_skip,
                                             const Tab &tab, int nlut, float inv_vmax, float alpha_stop, int px,
-                                            int py, unsigned long long &taken)
+                                            int py, uint32_t &taken, uint32_t &evaluated)
 {
     // ---- FP32 ray set-up, one rounding per operation, fixed order
     const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
@@ -258,7 +300,7 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
     const float nl1 = float(nlut - 1);
     const int jmax = nlut - 2;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-    int k = 0;
+    int k = 0, nev = 0;
     const int nn = int(n);
     bool occupied = skip ? marked() : true;  // the current cell's bit, refreshed at every crossing
     while (k < nn) {
@@ -285,11 +327,22 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
         const float fy = float(uint32_t(U[1])) * 2.3283064365386963e-10f;
         const float fz = float(uint32_t(U[2])) * 2.3283064365386963e-10f;
         const uint32_t za = tab.slice_at(z0i), zb = tab.slice_at(z1i);
-        const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
-        const float v000 = texel(atlas, za + ya + x0), v100 = texel(atlas, za + ya + x1);
-        const float v010 = texel(atlas, za + yb + x0), v110 = texel(atlas, za + yb + x1);
-        const float v001 = texel(atlas, zb + ya + x0), v101 = texel(atlas, zb + ya + x1);
-        const float v011 = texel(atlas, zb + yb + x0), v111 = texel(atlas, zb + yb + x1);
+        float v000, v100, v010, v110, v001, v101, v011, v111;
+        if constexpr (Tab::kGather) {
+            const bool dx = x1 != x0, dy = y1i != y0i;
+            gather_quad<T>(tab.tex, za, x0, y0i, dx, dy, v000, v100, v010, v110);
+            gather_quad<T>(tab.tex, zb, x0, y0i, dx, dy, v001, v101, v011, v111);
+        } else {
+            const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
+            v000 = texel(atlas, za + ya + x0);
+            v100 = texel(atlas, za + ya + x1);
+            v010 = texel(atlas, za + yb + x0);
+            v110 = texel(atlas, za + yb + x1);
+            v001 = texel(atlas, zb + ya + x0);
+            v101 = texel(atlas, zb + ya + x1);
+            v011 = texel(atlas, zb + yb + x0);
+            v111 = texel(atlas, zb + yb + x1);
+        }
         const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
         const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
         const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
@@ -304,6 +357,7 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
         C2 = fmaf(w, fmaf(fl, e1.z - e0.z, e0.z), C2);
         A += w;
         ++k;
+        if (kCount) ++nev;
         if (A >= alpha_stop) break;
         if (skip) {
             bool moved = false;
@@ -313,8 +367,27 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
             if (moved) occupied = marked();
         }
     }
-    taken += (unsigned long long)k;
+    taken += uint32_t(k);
+    if (kCount) evaluated += uint32_t(nev);
     return make_float4(C0, C1, C2, A);
+}
+
+// A per-thread 32-bit count that reached 2^31 goes to the 64-bit total (rare).
+__device__ __forceinline__ void flush_count(uint32_t &count, unsigned long long *total)
+{
+    if (count >= 0x80000000u) {
+        if (total) atomicAdd(total, (unsigned long long)count);
+        count = 0;
+    }
+}
+
+// The warp's 32-bit counts added to the 64-bit total by lane 0.
+__device__ __forceinline__ void warp_add_count(uint32_t count, unsigned long long *total)
+{
+    unsigned long long t = count;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0 && t && total) atomicAdd(total, t);
 }
 
 // ---- host side

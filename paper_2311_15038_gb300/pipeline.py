@@ -9,8 +9,10 @@ from dataclasses import dataclass
 
 import torch
 
-from . import (Slicemap, View, build_histogram, build_slicemap, find_container, image_entropy, mask_container,
-               render_views, select_threshold)
+from . import _lib
+from ._lib import MctpError
+from . import (BatchTuning, Slicemap, View, build_histogram, build_slicemap, find_container, image_entropy,
+               mask_container, render_batch, render_batch_workspace, render_views, select_threshold)
 
 
 @dataclass
@@ -28,6 +30,9 @@ class PreviewConfig:
     container: bool = False                 # remove the sample container first (Hough circle on slice 0)
     container_thr: int = 40                 # edge threshold in 8-bit grey units
     container_margin: int = 2               # voxels kept inside the found inner wall
+    renderer: str = "batch"                 # "batch": work-queue renderer (mctp_render_batch); "views": mctp_render_views
+    tuning: BatchTuning | None = None       # launch shape of the work-queue renderer (None: 8 x 4 tiles, chunk 1)
+    texture: bool = True                    # work-queue renderer: gather corners through atlas textures
 
 
 def turntable(n: int, size: int, level: int = 0, step: float = 0.5, elevation: float = 0.0,
@@ -57,6 +62,23 @@ class PreviewPipeline:
             self.masked = torch.empty((nz, ny, nx), dtype=dtype, device=self.device)
             self.circle = None
         nv = max(len(cfg.views), 1)
+        if cfg.renderer == "batch":
+            # the work-queue renderer: its bitmap and slice tables live in a workspace
+            # read through L1, 4 CTAs per SM, one tail; same images as render_views
+            self._vsm = [0] * len(cfg.views)
+            self._vlut = [0] * len(cfg.views)
+            nbw = render_batch_workspace([self.sm], cfg.views, self._vsm, self._vlut, 1)
+            self.workspace = torch.empty(max(nbw, 256), dtype=torch.uint8, device=self.device)
+            self.tuning = cfg.tuning or BatchTuning(8, 1, 0)
+            if cfg.texture:
+                for k in sorted({v.level for v in cfg.views}):
+                    try:
+                        self.sm.make_textures([k])
+                    except MctpError as e:
+                        if e.code != _lib.MCTP_ESIZE:  # an atlas past the gather limit renders from loads
+                            raise
+        elif cfg.renderer != "views":
+            raise ValueError("renderer must be 'batch' or 'views'")
         self.image_hist = torch.empty((nv, 256), dtype=torch.uint64, device=self.device)
         self.entropy = torch.empty(nv, dtype=torch.float64, device=self.device)
         self.best = torch.empty(1, dtype=torch.int32, device=self.device)
@@ -83,9 +105,29 @@ class PreviewPipeline:
             keep = self.keep
         mark("slicemap")
         build_slicemap(vol, c.bits, self.sm, keep, self.stream)
+        mark("texture")
+        self.sm.update_textures(self.stream)
         mark("render")
-        render_views(self.sm, c.views, lut, c.alpha_stop, self.images, self.samples, self.stream)
+        if c.renderer == "batch":
+            render_batch([self.sm], c.views, self._vsm, self._vlut, lut, c.alpha_stop, self.tuning, self.images,
+                         self.samples, self.workspace, self.stream)
+        else:
+            render_views(self.sm, c.views, lut, c.alpha_stop, self.images, self.samples, self.stream)
         mark("entropy")
         image_entropy(self.images, c.views, self.image_hist, self.entropy, self.best, self.stream)
         mark("end")
         return self.images, self.samples
+
+
+def autotune(pipe: PreviewPipeline, lut: torch.Tensor, reps: int = 2):
+    """Pick the work-queue renderer's launch shape for this pipeline's views by
+    timing candidates on its current slicemap (run one pass first)."""
+    from .batch import autotune_render
+    if pipe.cfg.renderer != "batch":
+        return None, {}
+    luts = lut if lut.dim() == 3 else lut.unsqueeze(0)
+    stream = pipe.stream or torch.cuda.current_stream(pipe.device)
+    best, timings = autotune_render([pipe.sm], pipe.cfg.views, pipe._vsm, pipe._vlut, luts, pipe.cfg.alpha_stop,
+                                    stream, reps, pipe.images, pipe.samples, pipe.workspace)
+    pipe.tuning = best
+    return best, timings

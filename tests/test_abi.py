@@ -239,7 +239,7 @@ def test_render_batch_rejects(lib):
     assert call(out=None) == -1
     for w, c, k in [(2, 1, 0), (64, 1, 0), (12, 1, 0), (8, 65, 0), (8, -1, 0), (8, 1, -1)]:
         assert call(tun=_lib.BatchTuning(w, c, k, 0)) == -1
-    assert call(tun=_lib.BatchTuning(8, 2, 0, 1)) == -1      # reserved must be 0
+    assert call(tun=_lib.BatchTuning(8, 2, 0, 2)) == -1      # unknown flag
 
 
 def test_render_batch_static_rejects_oversized_batch(lib):
@@ -327,3 +327,19 @@ def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_atlas_texture_rejects(lib):
+    """Argument checks of the atlas-texture calls, all before any CUDA call."""
+    s = _slicemap([(32, 32, 32), (16, 16, 16)])
+    out, h = ctypes.c_void_p(), ctypes.c_uint64()
+    assert lib.mctp_atlas_texture_create(ctypes.byref(s), 0, None, ctypes.byref(h)) == -1
+    assert lib.mctp_atlas_texture_create(ctypes.byref(s), 0, ctypes.byref(out), None) == -1
+    assert lib.mctp_atlas_texture_create(None, 0, ctypes.byref(out), ctypes.byref(h)) == -1
+    for level in (-1, 2):
+        assert lib.mctp_atlas_texture_create(ctypes.byref(s), level, ctypes.byref(out), ctypes.byref(h)) == -1
+        assert out.value is None and h.value == 0
+    bad = _slicemap([(32, 32, 32)], tiles=[(4, 4)])  # 16 tiles for 32 slices
+    assert lib.mctp_atlas_texture_create(ctypes.byref(bad), 0, ctypes.byref(out), ctypes.byref(h)) == -3
+    assert lib.mctp_atlas_texture_update(None, ctypes.byref(s), 0, None) == -1
+    assert lib.mctp_atlas_texture_destroy(None) == 0

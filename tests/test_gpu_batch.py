@@ -226,3 +226,38 @@ def test_batch_pipeline_graph_and_autotune(env):
         torch.cuda.synchronize(dev)
         assert torch.equal(pipe.images, eager)
         assert int(pipe.samples.item()) == eager_s
+
+
+def test_preview_pipeline_renderers_agree(env):
+    """PreviewPipeline renders through the work-queue launch with atlas
+    textures by default; its images, sample count and best view equal the
+    render_views path and the work-queue launch without textures, before and
+    after autotuning the launch shape."""
+    mctp, oracle, phantom, dev = env
+    from paper_2311_15038_gb300 import pipeline as pl
+    spec = phantom.VolumeSpec(150, 130, 90, bits=12, seed=21, n_ell=5)
+    vol = torch.from_numpy(phantom.generate_cpu(spec)).to(dev)
+    lut = up(phantom.ramp_lut(256), dev)
+    views = pl.turntable(5, 40, 0, 0.5, 15.0) + pl.turntable(3, 33, 1, 0.75, -30.0)
+    out = {}
+    for renderer, tex in (("views", False), ("batch-loads", False), ("batch", True)):
+        cfg = pl.PreviewConfig((150, 130, 90), 12, 4096, (64, 64, 48), 2, views, "otsu",
+                               renderer=renderer.split("-")[0], texture=tex)
+        pipe = pl.PreviewPipeline(cfg, torch.uint16, dev)
+        assert (pipe.sm.textures is not None) == tex
+        pipe.run(vol, lut)
+        torch.cuda.synchronize(dev)
+        out[renderer] = (pipe.images.clone(), int(pipe.samples.item()), int(pipe.best.item()))
+        if renderer == "batch":
+            best, timings = pl.autotune(pipe, lut, reps=1)
+            assert best in timings and pipe.tuning == best
+            pipe.run(vol, lut)
+            torch.cuda.synchronize(dev)
+            out["tuned"] = (pipe.images.clone(), int(pipe.samples.item()), int(pipe.best.item()))
+    ref = out["views"]
+    assert ref[1] > 0
+    for k in ("batch-loads", "batch", "tuned"):
+        assert torch.equal(out[k][0], ref[0]) and out[k][1:] == ref[1:], k
+    with pytest.raises(ValueError):
+        pl.PreviewPipeline(pl.PreviewConfig((150, 130, 90), 12, 4096, (64, 64, 48), 2, views, renderer="x"),
+                           torch.uint16, dev)
