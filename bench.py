@@ -197,11 +197,11 @@ def launches_per_step(wl, nviews, ntex):
     """Kernels of this library launched by one step: histogram, threshold
     selection, the level-0 slicemap kernel (levels 1-2 fused), one 2x2x2 kernel
     per further level, one max-grid kernel per level, one texture update per
-    textured level, the work-queue renderer (set-up kernel, one view-upload
-    kernel per 128 views, the render kernel), one image-histogram launch per
-    1024 views, the entropy and best-view kernels."""
+    textured level, the work-queue renderer (set-up kernel, depth-bounds
+    kernel, one view-upload kernel per 128 views, the render kernel), one
+    image-histogram launch per 1024 views, the entropy and best-view kernels."""
     nl = wl["nlevels"]
-    return (1 + 1 + 1 + max(0, nl - 3) + nl + ntex + 2 + (nviews + 127) // 128 + (nviews + 1023) // 1024 + 2)
+    return (1 + 1 + 1 + max(0, nl - 3) + nl + ntex + 3 + (nviews + 127) // 128 + (nviews + 1023) // 1024 + 2)
 
 
 def dist_setup():

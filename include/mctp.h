@@ -278,6 +278,10 @@ int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views, int32_t n
  *                 samples whose corners were fetched and looked up.
  * When every (slicemap, level) of the batch has an atlas texture
  * (sm->texture[level] != 0), corner quads are gathered through the textures.
+ * A set-up kernel rasterises, per view and 16 x 16 pixel tile, the depth
+ * range of the level's marked cells (max grid), and each ray marches only
+ * the samples in its tile's range (the others lie in unmarked cells): rays
+ * that meet no marked cell take no step.  The workspace holds the raster.
  * Everything is enqueued on `stream` (kernel launches and memsets only; no
  * host synchronisation), so a call can be captured in a CUDA graph.
  * Errors: MCTP_EINVAL (null pointers, an index out of range, bad view,

@@ -72,9 +72,11 @@ inline int num_sms()
 int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, const int32_t *view_slicemap,
                       const int32_t *view_lut, int32_t nviews, const float *luts_rgba, int32_t nluts, int32_t nlut,
                       float alpha_stop, const mctp_batch_tuning *tuning, float *out_rgba, const int64_t *out_offsets,
-                      uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s);
+                      uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s,
+                      bool depth_bounds);
 
-// Upper bound of the batch workspace over batches of at most max_views views.
+// Upper bound of the batch workspace over batches of at most max_views views
+// rendered without depth bounds.
 size_t batch_workspace_bound(const mctp_slicemap *sms, int32_t nsm, int32_t max_views);
 
 // 16-byte streaming load that bypasses L1 allocation (data read once).

@@ -3,15 +3,24 @@
 // A batch mixes slicemaps of any sizes, levels and transfer functions.  Work
 // is a queue of warp tiles (32 rays: warp_w x 32/warp_w pixels) over all views
 // in order; every warp takes `chunk` consecutive warp tiles at a time with one
-// atomic add on a counter, so no warp idles while others still march long
-// rays, and there is one tail for the whole batch rather than one per view.
+// atomic add on a counter (issued one grab ahead), so no warp idles while
+// others still march long rays, and there is one tail for the whole batch
+// rather than one per view.
 // Eight warp tiles form a super tile of about 16 x 16 pixels, so consecutive
 // grabs stay close together in the image and share texels in L1/L2.
 //
 // Per-view constants and per-(slicemap, level, transfer function) tables
 // (slice offsets of the atlas, the cell bitmap for empty-space skipping) are
 // built once per call into a caller-provided device workspace by small
-// set-up kernels, and read by the march through the read-only cache.  The
+// set-up kernels, and read by the march through the read-only cache.
+//
+// Depth bounds: a set-up kernel projects every marked cell of a view's level
+// into the view's image and records, per 16 x 16 pixel tile, the least and
+// greatest depth along the rays at which a marked cell lies.  A ray marches
+// only the samples between those depths (its first and last samples that can
+// reach a marked cell, with a margin); the samples before and after lie in
+// unmarked cells and add exactly nothing, so images and sample counts do not
+// change, while rays that meet no marked cell take no step at all.  The
 // march itself is the one of the single-call renderer (render_common.cuh), so
 // a view's image and sample count are bit-identical to rendering it alone.
 //
@@ -37,6 +46,7 @@ constexpr int kUploadViews = 128;
 constexpr int kPrepPairs = 256;
 constexpr size_t kLutSmemMax = 48 * 1024;  // all transfer functions go to shared memory up to this size
 constexpr size_t kAlign = 256;
+constexpr int kBoundsTile = 16;  // pixels per side of a depth-bounds tile
 
 // One (slicemap, level, transfer function) combination used by the batch.
 struct BatchPair {
@@ -57,8 +67,10 @@ struct BatchPair {
 struct BatchView {
     ViewParams vp;
     int32_t pair;
-    int32_t stiles_x;     // super tiles along x
-    uint32_t item_begin;  // first warp tile of this view in the queue
+    int32_t stiles_x;       // super tiles along x
+    uint32_t item_begin;    // first warp tile of this view in the queue
+    uint32_t bounds_begin;  // first depth-bounds tile of this view
+    int32_t btiles_x;       // depth-bounds tiles along x
     int32_t pad;
 };
 
@@ -87,8 +99,9 @@ struct BatchArgs {
     const float4 *luts;
     float *out;
     unsigned long long *samples;
-    unsigned int *counter;
+    unsigned int *counter;                  // the queue counter (workspace bytes 64..67)
     unsigned long long *counter_evaluated;  // workspace bytes 8..15
+    const uint32_t *bounds_lo, *bounds_hi;  // per depth-bounds tile; nullptr: no bounds
     int32_t nviews, nlut, nluts;
     uint32_t total_items;
     int32_t wx_log2;  // log2 warp_w
@@ -99,7 +112,7 @@ struct BatchArgs {
 __global__ void __launch_bounds__(kBatchThreads) batch_upload_kernel(const __grid_constant__ UploadArgs A)
 {
     static_assert(sizeof(BatchView) % 4 == 0, "word copy");
-    static_assert(sizeof(PrepArgs) <= 32000, "kernel parameter space");
+    static_assert(sizeof(PrepArgs) <= 32000 && sizeof(UploadArgs) <= 32000, "kernel parameter space");
     const uint32_t *src = reinterpret_cast<const uint32_t *>(A.view);
     uint32_t *dst = reinterpret_cast<uint32_t *>(A.dst + A.first);
     const int nw = A.count * int(sizeof(BatchView) / 4);
@@ -149,6 +162,79 @@ __global__ void __launch_bounds__(kBatchThreads) batch_prep_kernel(const __grid_
     }
 }
 
+// Block (x, y): bitmap words x, x + gridDim.x, ... of view y's level.  Each
+// marked cell c covers the level coordinates [8c - 1, 8c + 9] per axis (its
+// samples' positions, [8c, 8c + 8) or up to half a voxel past a face, with a
+// voxel of margin), a box in the world; the box's image footprint (one pixel
+// of margin) and its depth range along the view direction go to the tiles.
+// Views whose pair does not skip get the full range on every tile.
+__global__ void __launch_bounds__(kBatchThreads) batch_bounds_kernel(const BatchView *__restrict__ views,
+                                                                    const BatchPair *__restrict__ pairs,
+                                                                    int32_t nviews, uint32_t *__restrict__ lo,
+                                                                    uint32_t *__restrict__ hi)
+{
+    for (int vi = blockIdx.y; vi < nviews; vi += gridDim.y) {
+        const BatchView &BV = views[vi];
+        const ViewParams &V = BV.vp;
+        const BatchPair &PR = pairs[BV.pair];
+        const int btx = BV.btiles_x, bty = (V.H + kBoundsTile - 1) / kBoundsTile;
+        uint32_t *vlo = lo + BV.bounds_begin, *vhi = hi + BV.bounds_begin;
+        if (!PR.use_skip) {
+            for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < btx * bty; t += gridDim.x * blockDim.x) {
+                vlo[t] = 0u;
+                vhi[t] = __float_as_uint(3.0e38f);
+            }
+            continue;
+        }
+        const float s[3] = {V.N[0] / float(PR.mx), V.N[1] / float(PR.my), V.N[2] / float(PR.mz)};
+        const float invL = 1.0f / V.L;
+        const int nwords = PR.gy * PR.gz * PR.wpr;
+        for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+            uint32_t bits = __ldg(PR.occ + w);
+            if (!bits) continue;
+            const int r = w / PR.wpr, wx = w - r * PR.wpr;
+            const int cy = r % PR.gy, cz = r / PR.gy;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int cell[3] = {wx * 32 + b, cy, cz};
+                // extremes of <p - centre, e> over the box, for e = r, u, b
+                float xr[2] = {0.f, 0.f}, xu[2] = {0.f, 0.f}, xb[2] = {0.f, 0.f};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float p0 = (float(8 * cell[a] - 1) + 0.5f) * s[a] - V.c[a];
+                    const float p1 = (float(8 * cell[a] + 9) + 0.5f) * s[a] - V.c[a];
+                    xr[0] += fminf(p0 * V.r[a], p1 * V.r[a]);
+                    xr[1] += fmaxf(p0 * V.r[a], p1 * V.r[a]);
+                    xu[0] += fminf(p0 * V.u[a], p1 * V.u[a]);
+                    xu[1] += fmaxf(p0 * V.u[a], p1 * V.u[a]);
+                    xb[0] += fminf(p0 * V.b[a], p1 * V.b[a]);
+                    xb[1] += fmaxf(p0 * V.b[a], p1 * V.b[a]);
+                }
+                // pixel (px, py) looks along the line with sx = (px + 1/2) / W - 1/2,
+                // sy = 1/2 - (py + 1/2) / H, sx = <p - centre, r> / L, sy likewise with u
+                const float fx0 = (xr[0] * invL + 0.5f) * float(V.W) - 0.5f;
+                const float fx1 = (xr[1] * invL + 0.5f) * float(V.W) - 0.5f;
+                const float fy0 = (0.5f - xu[1] * invL) * float(V.H) - 0.5f;
+                const float fy1 = (0.5f - xu[0] * invL) * float(V.H) - 0.5f;
+                const float wmax = float(V.W) + 2.0f, hmax = float(V.H) + 2.0f;
+                const int px0 = max(int(ceilf(fminf(fmaxf(fx0, -2.0f), wmax))) - 1, 0);
+                const int px1 = min(int(floorf(fminf(fmaxf(fx1, -2.0f), wmax))) + 1, V.W - 1);
+                const int py0 = max(int(ceilf(fminf(fmaxf(fy0, -2.0f), hmax))) - 1, 0);
+                const int py1 = min(int(floorf(fminf(fmaxf(fy1, -2.0f), hmax))) + 1, V.H - 1);
+                if (px0 > px1 || py0 > py1) continue;
+                // depth along d = -b, plus L: positive inside the box
+                const uint32_t dlo = __float_as_uint(V.L - xb[1]), dhi = __float_as_uint(V.L - xb[0]);
+                for (int ty = py0 / kBoundsTile; ty <= py1 / kBoundsTile; ++ty)
+                    for (int tx = px0 / kBoundsTile; tx <= px1 / kBoundsTile; ++tx) {
+                        atomicMin(vlo + ty * btx + tx, dlo);
+                        atomicMax(vhi + ty * btx + tx, dhi);
+                    }
+            }
+        }
+    }
+}
+
 template <typename T, bool kLutShared, bool kGather, bool kCount>
 __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __grid_constant__ BatchArgs P)
 {
@@ -167,12 +253,15 @@ __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __
     uint32_t taken = 0, evaluated = 0;
     int v = -1;
     uint32_t vbegin = 0, vend = 0;
+    // The next grab is issued before the current chunk is marched, so the
+    // atomic's round trip overlaps the work instead of stalling the warp.
     const uint32_t chunk = uint32_t(P.chunk);
-    for (;;) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(P.counter, chunk);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= P.total_items) break;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(P.counter, chunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    while (base < P.total_items) {
+        uint32_t next = 0;
+        if (lane == 0) next = atomicAdd(P.counter, chunk);
         const uint32_t end = min(base + chunk, P.total_items);
         for (uint32_t item = base; item < end; ++item) {
             if (item >= vend) {
@@ -197,20 +286,27 @@ __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __
             const BatchPair &PR = P.pairs[BV.pair];
             const LevelGeom G{{PR.mx - 1, PR.my - 1, PR.mz - 1}, uint32_t(PR.pitch), PR.gy, PR.wpr};
             const float4 *lut = (kLutShared ? slut : P.luts) + int64_t(PR.lut) * P.nlut;
+            DepthRange range{false, 0u, 0u};
+            if (P.bounds_lo) {
+                const uint32_t bt = BV.bounds_begin + uint32_t(py / kBoundsTile) * uint32_t(BV.btiles_x) +
+                                    uint32_t(px / kBoundsTile);
+                range = DepthRange{true, __ldg(P.bounds_lo + bt), __ldg(P.bounds_hi + bt)};
+            }
             float4 acc;
             if constexpr (kGather) {
                 const GatherTables<kLutShared> tab{lut, PR.slice_off, PR.occ, cudaTextureObject_t(PR.tex)};
                 acc = march_ray<T, kCount>(BV.vp, static_cast<const T *>(PR.atlas), G, PR.use_skip != 0, tab, P.nlut,
-                                   PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated);
+                                           PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated, range);
             } else {
                 const CachedTables<kLutShared> tab{lut, PR.slice_off, PR.occ};
                 acc = march_ray<T, kCount>(BV.vp, static_cast<const T *>(PR.atlas), G, PR.use_skip != 0, tab, P.nlut,
-                                   PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated);
+                                           PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated, range);
             }
             reinterpret_cast<float4 *>(P.out + BV.vp.out_offset)[int64_t(py) * BV.vp.W + px] = acc;
             flush_count(taken, P.samples);
             if (kCount) flush_count(evaluated, P.counter_evaluated);
         }
+        base = __shfl_sync(0xffffffffu, next, 0);
     }
     warp_add_count(taken, P.samples);
     if (kCount) warp_add_count(evaluated, P.counter_evaluated);
@@ -230,19 +326,23 @@ auto pick_kernel(bool lut_shared, bool gather, bool count) -> void (*)(BatchArgs
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Workspace layout of a batch: the queue counter (bytes 0..3) and the count of
-// evaluated samples (bytes 8..15) in the first 256 bytes, view records, the queue
+// Workspace layout of a batch: the count of evaluated samples (bytes 8..15)
+// and the queue counter (bytes 64..67) in the first 256 bytes, view records, the queue
 // start of each view, pair records, then per pair its slice offsets and cell
 // bitmap.
 struct Plan {
     std::vector<std::tuple<int, int, int>> pairs;  // (slicemap, level, lut)
     std::vector<int> view_pair;
     std::vector<size_t> slice_at, occ_at;  // byte offsets of each pair's tables
+    std::vector<uint32_t> bounds_begin;    // first depth-bounds tile of each view
     size_t views_at = 0, begin_at = 0, pairs_at = 0, total = 0;
+    size_t bounds_lo_at = 0, bounds_hi_at = 0;  // 0: no depth bounds
+    uint64_t bounds_tiles = 0;
+    int max_words = 0;  // bitmap words of the largest level
 };
 
 int make_plan(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, const int32_t *view_sm,
-              const int32_t *view_lut, int32_t nviews, int32_t nluts, Plan &plan)
+              const int32_t *view_lut, int32_t nviews, int32_t nluts, bool bounds, Plan &plan)
 {
     if (!sms || nsm < 1 || nviews < 0 || nluts < 1) return MCTP_EINVAL;
     if (nviews > 0 && (!views || !view_sm || !view_lut)) return MCTP_EINVAL;
@@ -267,7 +367,7 @@ int make_plan(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, con
         }
         plan.view_pair[size_t(i)] = it->second;
     }
-    size_t at = kAlign;  // the queue counter
+    size_t at = kAlign;  // the counters
     plan.views_at = at;
     at = align_up(at + size_t(nviews) * sizeof(BatchView));
     plan.begin_at = at;
@@ -285,7 +385,23 @@ int make_plan(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, con
             const size_t wpr = ((size_t(sm.dims[k][0]) + c - 1) / c + 31) / 32;
             const size_t rows = ((size_t(sm.dims[k][1]) + c - 1) / c) * ((size_t(sm.dims[k][2]) + c - 1) / c);
             at = align_up(at + rows * wpr * sizeof(uint32_t));
+            plan.max_words = std::max(plan.max_words, int(rows * wpr));
         }
+    }
+    if (bounds && nviews > 0) {
+        plan.bounds_begin.resize(size_t(nviews));
+        uint64_t tiles = 0;
+        for (int i = 0; i < nviews; ++i) {
+            plan.bounds_begin[size_t(i)] = uint32_t(tiles);
+            tiles += uint64_t((views[i].width + kBoundsTile - 1) / kBoundsTile) *
+                     uint64_t((views[i].height + kBoundsTile - 1) / kBoundsTile);
+            if (tiles > (uint64_t(1) << 31)) return MCTP_ESIZE;
+        }
+        plan.bounds_tiles = tiles;
+        plan.bounds_lo_at = at;
+        at = align_up(at + size_t(tiles) * sizeof(uint32_t));
+        plan.bounds_hi_at = at;
+        at = align_up(at + size_t(tiles) * sizeof(uint32_t));
     }
     plan.total = at;
     return MCTP_OK;
@@ -301,7 +417,7 @@ extern "C" int mctp_render_batch_workspace(const mctp_slicemap *sms, int32_t nsm
     using namespace mctp;
     if (!bytes) return MCTP_EINVAL;
     Plan plan;
-    const int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, plan);
+    const int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, true, plan);
     if (rc != MCTP_OK) return rc;
     *bytes = plan.total;
     return MCTP_OK;
@@ -314,11 +430,12 @@ namespace mctp {
 int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, const int32_t *view_slicemap,
                       const int32_t *view_lut, int32_t nviews, const float *luts_rgba, int32_t nluts, int32_t nlut,
                       float alpha_stop, const mctp_batch_tuning *tuning, float *out_rgba, const int64_t *out_offsets,
-                      uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s)
+                      uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s,
+                      bool depth_bounds)
 {
     using namespace mctp::render;
     Plan plan;
-    int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, plan);
+    int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, depth_bounds, plan);
     if (rc != MCTP_OK) return rc;
     if (!luts_rgba || !out_rgba || nlut < 2 || nlut > kMaxLut) return MCTP_EINVAL;
     if (!(alpha_stop > 0.0f && alpha_stop <= 1.0f)) return MCTP_EINVAL;
@@ -414,6 +531,8 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
             B.pair = plan.view_pair[size_t(i)];
             B.stiles_x = (w.width + sw - 1) / sw;
             B.item_begin = uint32_t(items);
+            B.bounds_begin = plan.bounds_tiles ? plan.bounds_begin[size_t(i)] : 0u;
+            B.btiles_x = (w.width + kBoundsTile - 1) / kBoundsTile;
             items += uint64_t(B.stiles_x) * uint64_t((w.height + sh - 1) / sh) * 8u;
             out_off += int64_t(w.width) * w.height * 4;
             if (items > (uint64_t(1) << 31)) return MCTP_ESIZE;  // queue positions are 32-bit
@@ -431,8 +550,24 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
         }
     }
 
+    // ---- depth bounds of the marked cells per view tile
+    uint32_t *bounds_lo = nullptr, *bounds_hi = nullptr;
+    if (plan.bounds_tiles) {
+        bounds_lo = reinterpret_cast<uint32_t *>(ws + plan.bounds_lo_at);
+        bounds_hi = reinterpret_cast<uint32_t *>(ws + plan.bounds_hi_at);
+        const size_t nb = size_t(plan.bounds_tiles) * sizeof(uint32_t);
+        if (cudaMemsetAsync(bounds_lo, 0xff, nb, s) != cudaSuccess || cudaMemsetAsync(bounds_hi, 0, nb, s) != cudaSuccess)
+            return MCTP_ECUDA;
+        const int gx = std::max(1, std::min(64, (plan.max_words + kBatchThreads - 1) / kBatchThreads));
+        const int gy = std::min(nviews, 65535);
+        batch_bounds_kernel<<<dim3(unsigned(gx), unsigned(gy)), kBatchThreads, 0, s>>>(ws_views, ws_pairs, nviews,
+                                                                                       bounds_lo, bounds_hi);
+        rc = launch_status();
+        if (rc != MCTP_OK) return rc;
+    }
+
     // ---- the persistent march over the queue
-    if (cudaMemsetAsync(ws, 0, 16, s) != cudaSuccess) return MCTP_ECUDA;  // queue counter, evaluated samples
+    if (cudaMemsetAsync(ws, 0, kAlign, s) != cudaSuccess) return MCTP_ECUDA;  // evaluated samples, queue counters
     BatchArgs P{};
     P.views = ws_views;
     P.item_begin = ws_begin;
@@ -440,8 +575,10 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
     P.luts = luts;
     P.out = out_rgba;
     P.samples = reinterpret_cast<unsigned long long *>(samples_taken);
-    P.counter = reinterpret_cast<unsigned int *>(ws);
+    P.counter = reinterpret_cast<unsigned int *>(ws + 64);
     P.counter_evaluated = reinterpret_cast<unsigned long long *>(ws + 8);
+    P.bounds_lo = bounds_lo;
+    P.bounds_hi = bounds_hi;
     P.nviews = nviews;
     P.nlut = nlut;
     P.nluts = nluts;
@@ -498,7 +635,7 @@ extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mc
 {
     return mctp::render_batch_impl(sms, nsm, views, view_slicemap, view_lut, nviews, luts_rgba, nluts, nlut,
                                    alpha_stop, tuning, out_rgba, nullptr, samples_taken, workspace, workspace_bytes,
-                                   mctp::as_stream(stream));
+                                   mctp::as_stream(stream), /*depth_bounds=*/true);
 }
 
 // ---- batched rendering without a caller workspace

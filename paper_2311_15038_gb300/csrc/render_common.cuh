@@ -45,6 +45,7 @@ struct ViewParams {
     int32_t level;
     float sc_hi[3], sc_lo[3];  // M_a / N_a as an unevaluated float sum
     float inv_m[3];            // 1 / |dU| (0 when dU == 0)
+    float inv_d[3];            // 1 / d_a, d = -b, correctly rounded (0 when d_a == 0)
     long long dU[3];           // fixed-point step of the level coordinate per sample
     uint32_t qq[3], rr[3];     // 8 voxels (fixed point) = qq |dU| + rr (qq capped at 2^30)
     int32_t skip_ok;           // |dU| < 2^32 on every axis: the cell DDA runs in 32 bits
@@ -206,6 +207,15 @@ __device__ __forceinline__ void gather_quad(cudaTextureObject_t tex, uint32_t or
     v11 = dx ? (dy ? d : b) : (dy ? c : a);
 }
 
+// Depth range of the samples of a ray that can lie in a marked cell, from the
+// per-view raster of the marked cells (render_batch.cu): lo and hi are the
+// float bits of depth + L, depth = <p - centre, d> along the ray; lo > hi:
+// no marked cell on the ray.  Off: every sample may.
+struct DepthRange {
+    bool on;
+    uint32_t lo, hi;
+};
+
 // March the ray of pixel (px, py) of view V through a level; returns the
 // premultiplied (C, A), adds the number of samples taken to `taken` and the
 // number of them evaluated (not skipped as empty) to `evaluated` (kCount;
@@ -214,7 +224,8 @@ __device__ __forceinline__ void gather_quad(cudaTextureObject_t tex, uint32_t or
 template <typename T, bool kCount = false, class Tab>
 __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas, const LevelGeom &G, bool use_skip,
                                             const Tab &tab, int nlut, float inv_vmax, float alpha_stop, int px,
-                                            int py, uint32_t &taken, uint32_t &evaluated)
+                                            int py, uint32_t &taken, uint32_t &evaluated,
+                                            DepthRange range = DepthRange{false, 0u, 0u})
 {
     // ---- FP32 ray set-up, one rounding per operation, fixed order
     const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
@@ -230,7 +241,7 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
         o[a] = __fadd_rn(t2, __fmul_rn(V.L, V.b[a]));
         d[a] = -V.b[a];
         if (d[a] != 0.0f) {
-            const float inv = __frcp_rn(d[a]);
+            const float inv = V.inv_d[a];  // = __frcp_rn(d[a]), rounded once on the host
             const float s0 = __fmul_rn(__fsub_rn(0.0f, o[a]), inv);
             const float s1 = __fmul_rn(__fsub_rn(V.N[a], o[a]), inv);
             tmin = fmaxf(tmin, fminf(s0, s1));
@@ -242,6 +253,24 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
     int64_t n = 0;
     if (!miss && tmax > tmin) n = int64_t(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
     if (n <= 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nn = int(n);
+
+    // ---- samples [k0, kend) can reach a marked cell; the others have
+    // opacity exactly 0.  Sample k sits at depth tmin + (k + 1/2) Delta - L,
+    // so k = (depth + L - tmin) / Delta - 1/2; two samples of margin cover
+    // the rounding of this estimate (the raster already adds a voxel).
+    int k0 = 0, kend = nn;
+    if (range.on) {
+        if (range.lo > range.hi) {
+            taken += uint32_t(nn);
+            return make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float inv_d = 1.0f / V.delta;
+        const float klo = (__uint_as_float(range.lo) - tmin) * inv_d - 2.5f;
+        const float khi = (__uint_as_float(range.hi) - tmin) * inv_d + 2.5f;
+        k0 = int(fminf(fmaxf(klo, 0.0f), float(nn)));
+        kend = int(fminf(fmaxf(khi, 0.0f), float(nn - 1))) + 1;
+    }
 
     // ---- fixed-point level coordinates of sample 0; the step is per view
     long long U0[3];
@@ -261,7 +290,7 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
     uint32_t ee[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        cc[a] = min(max(int(U0[a] >> 32), 0), Mm1[a]) >> 3;
+        cc[a] = min(max(int((U0[a] + (long long)k0 * dU[a]) >> 32), 0), Mm1[a]) >> 3;  // cell of sample k0
         nxt[a] = kInf;
         ee[a] = 0;
         const int last = Mm1[a] >> 3;
@@ -300,15 +329,14 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
     const float nl1 = float(nlut - 1);
     const int jmax = nlut - 2;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-    int k = 0, nev = 0;
-    const int nn = int(n);
+    int k = k0, nev = 0;
     bool occupied = skip ? marked() : true;  // the current cell's bit, refreshed at every crossing
-    while (k < nn) {
+    while (k < kend) {
         if (!occupied) {
             // an empty cell: its samples have opacity exactly 0; jump to the
             // first sample of the next cell
             const int kn = min(min(nxt[0], nxt[1]), nxt[2]);
-            if (kn >= nn) { k = nn; break; }
+            if (kn >= kend) break;
             k = kn;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -367,6 +395,7 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
             if (moved) occupied = marked();
         }
     }
+    if (A < alpha_stop) k = nn;  // not stopped early: every sample was taken (the rest are empty)
     taken += uint32_t(k);
     if (kCount) evaluated += uint32_t(nev);
     return make_float4(C0, C1, C2, A);
@@ -431,6 +460,8 @@ inline void fill_view(const mctp_slicemap *sm, const mctp_view &w, ViewParams &V
         V.dU[a] = llrint(double(V.delta) * double(-V.b[a]) * sc * 4294967296.0);
         const long long m = V.dU[a] < 0 ? -V.dU[a] : V.dU[a];
         V.inv_m[a] = m ? float(1.0 / double(m)) : 0.0f;
+        const float da = -V.b[a];
+        V.inv_d[a] = da != 0.0f ? 1.0f / da : 0.0f;  // IEEE single division: the device's __frcp_rn(da)
         const long long q = m ? (8LL << 32) / m : 0;
         V.qq[a] = uint32_t(std::min<long long>(q, 1LL << 30));
         V.rr[a] = uint32_t(m ? (8LL << 32) - q * m : 0);

@@ -261,3 +261,33 @@ def test_preview_pipeline_renderers_agree(env):
     with pytest.raises(ValueError):
         pl.PreviewPipeline(pl.PreviewConfig((150, 130, 90), 12, 4096, (64, 64, 48), 2, views, renderer="x"),
                            torch.uint16, dev)
+
+
+def test_depth_bounds_edge_cases(env):
+    """The per-tile depth bounds of the marked cells: a small off-centre object
+    (most rays meet no marked cell), views along the axes and straight down,
+    steps from 0.05 to 64 voxels (cell skipping off at the largest), 1 x 1 and
+    ragged image sizes, a single-level slicemap at both ends of u8: all equal
+    to render_views, image and sample count."""
+    mctp, oracle, phantom, dev = env
+    vol = np.zeros((40, 56, 72), np.uint8)
+    vol[30:36, 8:15, 50:61] = 200   # a small block near a corner
+    vol[2:4, 40:42, 3:5] = 90
+    sm = mctp.Slicemap.allocate((72, 56, 40), (36, 28, 20), 2, torch.uint8, 8, dev)
+    mctp.build_slicemap(up(vol, dev), 8, sm, None)
+    luts = up(np.stack(phantom.preset_luts()[:2]), dev)
+    views = []
+    for az, el in [(0.0, 0.0), (90.0, 0.0), (180.0, 0.0), (270.0, 0.0), (0.0, 90.0), (0.0, -90.0), (33.0, 71.0)]:
+        for step in (0.05, 0.5, 1.0, 64.0):
+            for (w, h) in ((1, 1), (37, 23), (64, 64)):
+                views.append(mctp.View(az, el, w, h, int(step > 0.9), step))
+    n = len(views)
+    vsm, vlut = [0] * n, [i % 2 for i in range(n)]
+    ref, ref_s = _alone(mctp, [sm], views, vsm, vlut, luts)
+    for tun in (mctp.BatchTuning(8, 1, 0), mctp.BatchTuning(32, 2, 0), mctp.BatchTuning(4, 3, 0)):
+        flat, smp, _ = mctp.render_batch([sm], views, vsm, vlut, luts, 0.99, tun)
+        assert torch.equal(flat[:ref.numel()], ref) and int(smp.item()) == ref_s, tun
+    sm.make_textures()
+    sm.update_textures()
+    flat, smp, _ = mctp.render_batch([sm], views, vsm, vlut, luts, 0.99)
+    assert torch.equal(flat[:ref.numel()], ref) and int(smp.item()) == ref_s
