@@ -96,7 +96,8 @@ def workload(name: str):
     if name == "serve":
         specs = phantom.serve_specs(200)
         return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=2, nviews=1,
-                    size=512, az_step=0.0, rates=(1000.0, 2500.0, 5000.0, 7500.0, 10000.0, 12500.0), requests=1500,
+                    size=512, az_step=0.0, rates=(1000.0, 2500.0, 5000.0, 7500.0, 10000.0, 12500.0, 15000.0, 20000.0),
+                    requests=1500,
                     desc="serve: 200 resident u8 cubes, edge ~U{256..1024} (%.1f GB), 256 bins, Otsu, slicemap "
                          "levels 256^3/128^3, Poisson requests 512^2|1024^2, az U[0,360), el U[-60,60], LUT from "
                          "8 presets, step 0.5, level 0" % (sum(sp.nbytes for sp in specs) / 1e9))

@@ -68,15 +68,19 @@ inline int num_sms()
     return n;
 }
 
+// Depth bounds of render_batch_impl: off, on (the workspace must hold them),
+// or on when the workspace has room for them.
+constexpr int kBoundsOff = 0, kBoundsOn = 1, kBoundsIfRoom = 2;
+
 // mctp_render_batch with optional per-view output offsets (render_batch.cu).
 int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, const int32_t *view_slicemap,
                       const int32_t *view_lut, int32_t nviews, const float *luts_rgba, int32_t nluts, int32_t nlut,
                       float alpha_stop, const mctp_batch_tuning *tuning, float *out_rgba, const int64_t *out_offsets,
                       uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s,
-                      bool depth_bounds);
+                      int depth_bounds);
 
-// Upper bound of the batch workspace over batches of at most max_views views
-// rendered without depth bounds.
+// Upper bound of the batch workspace over batches of at most max_views views,
+// with room for the depth bounds of views of up to 1024 x 1024 pixels.
 size_t batch_workspace_bound(const mctp_slicemap *sms, int32_t nsm, int32_t max_views);
 
 // 16-byte streaming load that bypasses L1 allocation (data read once).

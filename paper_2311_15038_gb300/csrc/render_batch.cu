@@ -431,12 +431,17 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
                       const int32_t *view_lut, int32_t nviews, const float *luts_rgba, int32_t nluts, int32_t nlut,
                       float alpha_stop, const mctp_batch_tuning *tuning, float *out_rgba, const int64_t *out_offsets,
                       uint64_t *samples_taken, void *workspace, size_t workspace_bytes, cudaStream_t s,
-                      bool depth_bounds)
+                      int depth_bounds)
 {
     using namespace mctp::render;
     Plan plan;
-    int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, depth_bounds, plan);
+    int rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, depth_bounds != kBoundsOff, plan);
     if (rc != MCTP_OK) return rc;
+    if (depth_bounds == kBoundsIfRoom && workspace_bytes < plan.total) {
+        plan = Plan();
+        rc = make_plan(sms, nsm, views, view_slicemap, view_lut, nviews, nluts, false, plan);
+        if (rc != MCTP_OK) return rc;
+    }
     if (!luts_rgba || !out_rgba || nlut < 2 || nlut > kMaxLut) return MCTP_EINVAL;
     if (!(alpha_stop > 0.0f && alpha_stop <= 1.0f)) return MCTP_EINVAL;
     if ((reinterpret_cast<uintptr_t>(luts_rgba) & 15) || (reinterpret_cast<uintptr_t>(out_rgba) & 15))
@@ -621,8 +626,9 @@ size_t batch_workspace_bound(const mctp_slicemap *sms, int32_t nsm, int32_t max_
             per_pair = std::max(per_pair, t);
         }
     const size_t v = size_t(std::max(max_views, 0));
+    const size_t tiles = (size_t(1024) / kBoundsTile + 1) * (size_t(1024) / kBoundsTile + 1);  // a 1024^2 view
     return kAlign + align_up(v * sizeof(BatchView)) + align_up((v + 1) * sizeof(uint32_t)) +
-           align_up(v * sizeof(BatchPair)) + v * per_pair;
+           align_up(v * sizeof(BatchPair)) + v * per_pair + 2 * align_up(v * tiles * sizeof(uint32_t));
 }
 
 }  // namespace mctp
@@ -635,7 +641,7 @@ extern "C" int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mc
 {
     return mctp::render_batch_impl(sms, nsm, views, view_slicemap, view_lut, nviews, luts_rgba, nluts, nlut,
                                    alpha_stop, tuning, out_rgba, nullptr, samples_taken, workspace, workspace_bytes,
-                                   mctp::as_stream(stream), /*depth_bounds=*/true);
+                                   mctp::as_stream(stream), mctp::kBoundsOn);
 }
 
 // ---- batched rendering without a caller workspace

@@ -174,7 +174,7 @@ bool mctp_server::launch(Slot &slot, std::vector<uint64_t> &batch)
         rc = mctp::render_batch_impl(sms.data(), int32_t(sms.size()), v.data(), vsm.data(), vlut.data(), n, luts,
                                      nluts, nlut, alpha_stop, &params.tuning, reinterpret_cast<float *>(arena),
                                      off.data(), slot.d_samples, slot.workspace, ws_bytes, slot.stream,
-                                     /*depth_bounds=*/false);
+                                     mctp::kBoundsIfRoom);
     }
     if (rc == MCTP_OK &&
         cudaMemcpyAsync(slot.h_samples, slot.d_samples, sizeof(uint64_t), cudaMemcpyDeviceToHost, slot.stream) !=
