@@ -344,8 +344,9 @@ int mctp_render_batch_static(const mctp_slicemap *sms, int32_t nsm, const mctp_v
 /*
  * Serving (an extension of this library: the paper's server renders previews
  * on request and streams them to clients, Sec. III-C).  A server keeps the
- * given slicemaps and transfer functions (caller memory, kept alive until
- * destroy) and renders requests as they arrive:
+ * given slicemaps, their atlas textures and the transfer functions (caller
+ * memory and objects, kept alive until destroy) and renders requests as they
+ * arrive:
  *   - requests are admitted in arrival order while their image fits in the
  *     free part of `arena` (caller device memory, 256-byte aligned; the
  *     server's per-stream counters and batch workspaces come first, the image
@@ -354,7 +355,9 @@ int mctp_render_batch_static(const mctp_slicemap *sms, int32_t nsm, const mctp_v
  *     of up to max_batch_views and launches each as one mctp_render_batch
  *     launch on a free stream (up to max_inflight streams); requests that
  *     arrive while batches are on the device join the next batch, which
- *     starts as soon as a stream is free (continuous batching);
+ *     starts as soon as a stream is free (continuous batching); each
+ *     stream's workspace has room for the depth bounds of views up to
+ *     1024 x 1024 pixels, and a batch with larger views renders without them;
  *   - MCTP_SERVE_PER_VIEW: one mctp_render_views launch per request, in
  *     arrival order (the plain per-view baseline);
  *   - a request's image is bit-identical to rendering its view alone with
