@@ -101,6 +101,12 @@ def workload(name: str):
                     desc="serve: 200 resident u8 cubes, edge ~U{256..1024} (%.1f GB), 256 bins, Otsu, slicemap "
                          "levels 256^3/128^3, Poisson requests 512^2|1024^2, az U[0,360), el U[-60,60], LUT from "
                          "8 presets, step 0.5, level 0" % (sum(sp.nbytes for sp in specs) / 1e9))
+    if name == "batch8":
+        specs = phantom.batch_specs(64)[:8]
+        return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=1, nviews=12,
+                    size=512, az_step=30.0, elevation=20.0,
+                    desc="batch8 (profiling): the first 8 volumes of the batch workload (%.1f GB), otherwise "
+                         "the same" % (sum(sp.nbytes for sp in specs) / 1e9))
     if name == "batch":
         specs = phantom.batch_specs(64)
         return dict(specs=specs, spec=specs[0], bits=8, nbins=256, level0=(256, 256, 256), nlevels=1, nviews=12,
@@ -1094,7 +1100,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mctp", choices=["mctp", "reference"])
     ap.add_argument("--workload", default="full",
-                    choices=["full", "mid", "slab", "small", "batch", "serve", "fit", "thresholds"])
+                    choices=["full", "mid", "slab", "small", "batch", "batch8", "serve", "fit", "thresholds"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--render-tuning", default=None, metavar="WARP_W,CHUNK,CTAS",
                     help="fixed launch shape of the work-queue renderer (default: autotuned after warm-up)")
@@ -1102,7 +1108,7 @@ def main():
     wl = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)
-    if args.workload == "batch":
+    if args.workload in ("batch", "batch8"):
         return run_batch(args, wl)
     if args.workload == "serve":
         return run_serve(args, wl)
