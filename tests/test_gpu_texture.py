@@ -199,3 +199,51 @@ def test_evaluated_count(env):
     bare = sm.without_maxgrid()
     _, smp, ws = mctp.render_batch([bare], views, vsm, vlut, luts_dev, 0.99, mctp.BatchTuning(count_evaluated=True))
     assert mctp.batch_samples_evaluated(ws) == int(smp.item())  # no skipping: every sample is evaluated
+
+
+def test_evaluated_count_matches_marked_samples(env):
+    """The evaluated-sample count is the number of samples whose lower corner
+    lies in a marked cell, and the sample count is the sum of the rays'
+    n: both checked against a host model of the rays (FP32 set-up as the
+    kernel, FP64 sample positions) with a transfer function too faint to stop
+    a ray, so every ray takes all of its samples."""
+    mctp, oracle, phantom, dev = env
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from ray_model import rays
+    src = (72, 64, 56)
+    dims = [(36, 32, 28), (18, 16, 14)]
+    sm = _build(env, phantom.VolumeSpec(*src, bits=8, seed=81, n_ell=5), dims, 8)
+    faint = phantom.ramp_lut(256).copy()
+    faint[:, 3] *= 0.02  # entry 0 transparent, every other entry slightly opaque: the skip threshold is 0
+    luts_dev = up(faint[None], dev)
+    views = [mctp.View(az, el, 40, 30, lv, st) for az, el, lv, st in
+             [(0.0, 0.0, 0, 0.5), (37.0, 21.0, 0, 0.5), (120.0, -50.0, 1, 0.7), (0.0, 90.0, 0, 1.0),
+              (250.0, 10.0, 1, 0.5)]]
+    n = len(views)
+    sm.make_textures()
+    sm.update_textures()
+    flat, smp, ws = mctp.render_batch([sm], views, [0] * n, [0] * n, luts_dev, 1.0,
+                                      mctp.BatchTuning(8, 1, 0, count_evaluated=True))
+    ev = mctp.batch_samples_evaluated(ws)
+    taken = int(smp.item())
+    N = np.array(src)
+    want_taken, want_ev = 0, 0
+    for v in views:
+        M = np.array(dims[v.level])
+        R = rays(N, M, v.azimuth_deg, v.elevation_deg, v.width, v.height, v.step)
+        occ = sm.maxgrids[v.level].cpu().numpy() > 0  # [gz][gy][gx]
+        sc = M / N
+        kmax = int(R["n"].max())
+        k = np.arange(kmax)
+        t = R["tmin"][..., None].astype(np.float64) + (k + 0.5) * float(R["delta"])
+        q = (R["o"][..., None, :].astype(np.float64) + t[..., None] * R["d"].astype(np.float64)) * sc - 0.5
+        cell = np.clip(np.floor(q).astype(np.int64), 0, M - 1) >> 3
+        valid = k[None, None, :] < R["n"][..., None]
+        marked = occ[cell[..., 2], cell[..., 1], cell[..., 0]]
+        want_taken += int(R["n"].sum())
+        want_ev += int((marked & valid).sum())
+    assert taken == want_taken
+    assert ev == want_ev
+    assert 0 < ev < taken
