@@ -218,6 +218,23 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest value of x over all ranks (x itself on one rank): the job's
+    time is the slowest replica's."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, steps: int, ws: int, seconds: float) -> float:
+    """Whole-job throughput of N replicas (weak scaling): every rank processes
+    the same units per step, and the job takes the slowest rank's time."""
+    return units_per_rank_step * steps * ws / seconds
+
+
 # --------------------------------------------------------------- CPU oracle
 
 def oracle_sample(wl, slab=None, npix=8192):
@@ -381,10 +398,7 @@ def run_gpu(args, wl):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    if ws > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, ws, dev)
     step_ms = [a.elapsed_time(b) for a, b in step_events]
     stage_ms = {}
     for i, name in enumerate(stages):
@@ -409,10 +423,7 @@ def run_gpu(args, wl):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws, dev)
 
     if rank != 0:
         torch.distributed.barrier()
@@ -451,8 +462,7 @@ def run_gpu(args, wl):
                               frac=ach / fp32_peak, ms=stage_ms[name], traffic=traffic.get(name))
     roof["render"]["compulsory_hbm_gbs"] = wl["nviews"] * level0_bytes / (stage_ms["render"] / 1e3) / 1e9
     dominant = max(stage_ms, key=stage_ms.get)
-    steps_total = samples_per_step * args.steps * ws
-    value = steps_total / elapsed
+    value = job_rate(samples_per_step, args.steps, ws, elapsed)
     best_view = int(pipe.best.item())
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
@@ -623,10 +633,7 @@ def run_batch(args, wl):
     elapsed = t0.elapsed_time(t1) / 1e3
     assert int(pipe.samples.item()) == samples_per_step
     assert torch.equal(pipe.images, ref_images)
-    if ws > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, ws, dev)
     step_ms = [a.elapsed_time(b) for a, b in step_events]
 
     # ---- end to end: every volume from pinned host memory, every image back
@@ -652,10 +659,7 @@ def run_batch(args, wl):
     torch.cuda.synchronize(dev)
     e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
     del hosts
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws, dev)
     if rank != 0:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -669,7 +673,7 @@ def run_batch(args, wl):
     ach = FP32_FLOPS_PER_SAMPLE * evaluated_per_step / render_s / 1e12
     roof = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak, kernel="render",
                 ms=stage_ms["render"], traffic=None, peak_source="FP32 issue rate at the maximum SM clock")
-    value = samples_per_step * args.steps * ws / elapsed
+    value = job_rate(samples_per_step, args.steps, ws, elapsed)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
         ms_per_step=elapsed * 1e3 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -904,10 +908,7 @@ def run_fit(args, wl):
     torch.cuda.synchronize(dev)
     e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
     loss1 = fit.evaluate()
-    if ws > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, ws, dev)
 
     def psnr(loss):  # loss = mean squared error over RGBA
         return float(10.0 * np.log10(1.0 / max(loss, 1e-30)))
@@ -921,7 +922,7 @@ def run_fit(args, wl):
     it_s = elapsed / args.steps
     ach = FP32_FLOPS_PER_SAMPLE * samples_fwd / (stage_ms["forward"] / 1e3) / 1e12
     line = dict(
-        metric=METRIC, value=samples_fwd * args.steps * ws / elapsed, unit=UNIT, n_gpus=ws, steps=args.steps,
+        metric=METRIC, value=job_rate(samples_fwd, args.steps, ws, elapsed), unit=UNIT, n_gpus=ws, steps=args.steps,
         warmup=args.warmup, ms_per_step=it_s * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32", data="synthetic",
         config=dict(workload=wl["desc"], l2="fitted volume 8.4 MB (L2-resident); targets 100 MB",
