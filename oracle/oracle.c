@@ -562,7 +562,7 @@ int orc_ray_params(int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny, i
 /*
  * Per-cell maximum of a slicemap level, the occupancy data that lets a
  * renderer skip samples whose transfer-function opacity is exactly zero (an
- * acceleration structure of this build; the paper has none).  Cell
+ * acceleration structure of this library; the paper has none).  Cell
  * (cx, cy, cz) of edge `cell` covers level voxels [cell*c, cell*c + cell] per
  * axis (one voxel beyond the cell, clamped to the level): every voxel a
  * trilinear sample whose lower corner lies in the cell can touch.

@@ -1,7 +1,7 @@
 """Pins of the CPU oracle's renderer (server-side rendering, Sec. III-C).
 
 The renderer's definition (camera, FP32 ray setup, trilinear sampling, linear
-transfer function, front-to-back compositing with early exit) is this build's
+transfer function, front-to-back compositing with early exit) is this library's
 reading, since the paper only names the step.  It is pinned by:
 * the Beer-Lambert closed form A = 1 - (1 - a)^n on a constant volume,
 * axis-aligned views along each of the three axes, compared with a
