@@ -219,9 +219,10 @@ int launch_hist(const T *base, int64_t n, int bits, int nbins, uint64_t *hist, u
         kern<<<unsigned(grid), kHistThreads, smem, s>>>(base, n, head, nvec, shift, limit, nbins, h, ov);
         return launch_status();
     }
-    // copies: as many private sub-histograms as fit in ~64 KB, up to one per warp
+    // copies: as many private sub-histograms as fit in 32 KB, up to one per warp (more copies
+    // and fewer CTAs per SM measured slower: 4096 bins, 4 copies 2.955 ms, 2 copies 2.879 ms)
     int copies = 1;
-    while (copies < kHistThreads / 32 && size_t(copies * 2) * nbins * 4 <= 65536) copies *= 2;
+    while (copies < kHistThreads / 32 && size_t(copies * 2) * nbins * 4 <= 32768) copies *= 2;
     const size_t smem = size_t(copies) * nbins * 4;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(base);
     int64_t head = int64_t(((16 - (addr & 15)) & 15) / sizeof(T));
