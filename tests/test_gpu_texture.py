@@ -250,3 +250,28 @@ def test_evaluated_count_matches_marked_samples(env):
     assert taken == want_taken
     assert ev == want_ev
     assert 0 < ev < taken
+
+
+def test_texture_16bit_and_global_luts(env):
+    """Full 16-bit grey values (up to 65535) gathered through u16 textures,
+    with 4096-entry transfer functions too large for shared memory (the
+    variant that reads them through the cache): equal to loads."""
+    mctp, oracle, phantom, dev = env
+    spec = phantom.VolumeSpec(90, 70, 64, bits=16, seed=91, n_ell=5, n_cyl=8)
+    vol = phantom.generate_cpu(spec)
+    assert vol.max() > 4096
+    dims = [(64, 48, 32), (32, 24, 16)]
+    sm = mctp.Slicemap.allocate((90, 70, 64), dims[0], 2, torch.uint16, 16, dev)
+    mctp.build_slicemap(up(vol, dev), 16, sm, None)
+    rng = np.random.default_rng(12)
+    luts = np.stack(phantom.preset_luts(4096, count=3))
+    luts[1, :, 3] = rng.uniform(0, 0.2, 4096).astype(np.float32)  # nonzero everywhere: no skipping
+    luts_dev = up(luts, dev)
+    views = _views(mctp, 2, seed=13)
+    vsm = [0] * len(views)
+    ref, ref_s = _render(mctp, [sm], views, vsm, luts_dev)
+    sm.make_textures()
+    sm.update_textures()
+    for tun in (mctp.BatchTuning(8, 1, 0), mctp.BatchTuning(16, 4, 0)):
+        got, got_s = _render(mctp, [sm], views, vsm, luts_dev, tun)
+        assert torch.equal(got, ref) and got_s == ref_s, tun
