@@ -120,3 +120,27 @@ def test_submit_rejects_image_larger_than_heap(env):
             srv.submit(mctp.View(0.0, 0.0, 512, 512, 0, 0.5), 0, 0)
         with pytest.raises(mctp.MctpError):
             srv.submit(mctp.View(0.0, 0.0, 8, 8, 5, 0.5), 0, 0)  # level out of range
+
+
+def test_served_with_textures_and_depth_bounds(env):
+    """Slicemaps with atlas textures: the batched server gathers corners and
+    marches within each tile's depth bounds when its workspace has room for
+    them (views up to 1024 x 1024), and without them for larger views; every
+    image still equals rendering its view alone with loads."""
+    import dataclasses
+    mctp, serve, sms, luts, dev = env
+    tex = [dataclasses.replace(sm, textures=None).make_textures() for sm in sms]
+    for t in tex:
+        t.update_textures()
+    reqs = _requests(mctp, tex, 60, seed=7)
+    big = [(mctp.View(30.0 + 50.0 * i, 10.0, 1100, 1100, 0, 0.5), i % len(sms), i) for i in range(2)]
+    for batch, rq in ((32, reqs), (2, big)):
+        with serve.Server(tex, luts, 256 << 20, "batched", batch, 2) as srv:
+            got = _serve_all(srv, rq)
+            st = srv.stats()
+        total = 0
+        for i, req in enumerate(rq):
+            ref, smp = _alone(mctp, sms, luts, req)
+            total += smp
+            assert torch.equal(got[i][1], ref), f"request {i} of the {batch}-view server differs"
+        assert st["samples"] == total
