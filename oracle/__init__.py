@@ -65,11 +65,15 @@ def _L():
         lib.orc_mask_circle.argtypes = [C_VP, ctypes.c_int, C_I64, C_I64, C_I64, C_I32, C_I32, C_I32, C_VP]
         lib.orc_render_dense.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
                                                                ctypes.POINTER(View), C_VP, C_I64, C_VP, C_VP]
+        lib.orc_render_dense_band.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
+                                                                    ctypes.c_double, ctypes.POINTER(View), C_VP,
+                                                                    C_I64, C_VP, C_VP, C_VP, C_VP]
         lib.orc_render_dense_grad.argtypes = [C_VP] + [C_I64] * 6 + [C_VP, ctypes.c_int, ctypes.c_double,
-                                                                    ctypes.POINTER(View), C_VP, C_VP, C_VP]
+                                                                    ctypes.POINTER(View), C_VP, C_VP, C_VP,
+                                                                    C_VP, C_VP]
         for f in ("orc_histogram", "orc_otsu", "orc_its", "orc_keep_threshold", "orc_keep_topslab",
                   "orc_filter", "orc_downsample", "orc_atlas_pack", "orc_render", "orc_ray_params",
-                  "orc_entropy", "orc_maxgrid", "orc_render_dense", "orc_render_dense_grad",
+                  "orc_entropy", "orc_maxgrid", "orc_render_dense", "orc_render_dense_band", "orc_render_dense_grad",
                   "orc_image_histogram", "orc_hough_circle", "orc_mask_circle"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -268,9 +272,31 @@ def render_dense(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el: floa
     return rgba, ns
 
 
+def render_dense_band(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el: float, width: int,
+                      height: int, step: float = 0.5, alpha_stop: float = 0.99, eps: float = 1e-4):
+    """FP64 dense render with the early-exit band: dict(rgba, lo, hi [H][W][4], nsamp [H][W][3]);
+    lo / hi stop at alpha_stop -/+ eps."""
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    mz, my, mx = vol.shape
+    nx, ny, nz = src_dims
+    lut = np.ascontiguousarray(lut, dtype=np.float64)
+    v = View(az, el, width, height, step)
+    npix = width * height
+    rgba, lo, hi = (np.zeros((npix, 4), np.float64) for _ in range(3))
+    ns = np.zeros((npix, 3), np.uint64)
+    _check(_L().orc_render_dense_band(_p(vol), mx, my, mz, nx, ny, nz, _p(lut), lut.shape[0], alpha_stop, eps,
+                                      ctypes.byref(v), None, npix, _p(rgba), _p(lo), _p(hi), _p(ns)),
+           "render_dense_band")
+    shape = (height, width, 4)
+    return dict(rgba=rgba.reshape(shape), lo=lo.reshape(shape), hi=hi.reshape(shape),
+                nsamp=ns.reshape(height, width, 3))
+
+
 def render_dense_grad(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el: float, width: int,
-                      height: int, g_rgba: np.ndarray, step: float = 0.5, alpha_stop: float = 0.99):
-    """Gradient of sum(g_rgba * render_dense(...)) -> (g_vol like vol, g_lut like lut), FP64."""
+                      height: int, g_rgba: np.ndarray, step: float = 0.5, alpha_stop: float = 0.99,
+                      magnitudes: bool = False):
+    """Gradient of sum(g_rgba * render_dense(...)) -> (g_vol like vol, g_lut like lut), FP64.
+    With magnitudes=True also the per-element sums of |terms| -> (g_vol, g_lut, mag_vol, mag_lut)."""
     vol = np.ascontiguousarray(vol, dtype=np.float64)
     mz, my, mx = vol.shape
     nx, ny, nz = src_dims
@@ -278,10 +304,14 @@ def render_dense_grad(vol: np.ndarray, src_dims, lut: np.ndarray, az: float, el:
     g = np.ascontiguousarray(g_rgba, dtype=np.float64).reshape(height * width * 4)
     gv = np.zeros_like(vol)
     gl = np.zeros_like(lut)
+    mv = np.zeros_like(vol) if magnitudes else None
+    ml = np.zeros_like(lut) if magnitudes else None
     v = View(az, el, width, height, step)
     _check(_L().orc_render_dense_grad(_p(vol), mx, my, mz, nx, ny, nz, _p(lut), lut.shape[0], alpha_stop,
-                                      ctypes.byref(v), _p(g), _p(gv), _p(gl)), "render_dense_grad")
-    return gv, gl
+                                      ctypes.byref(v), _p(g), _p(gv), _p(gl),
+                                      _p(mv) if magnitudes else None, _p(ml) if magnitudes else None),
+           "render_dense_grad")
+    return (gv, gl, mv, ml) if magnitudes else (gv, gl)
 
 
 def image_histogram(rgba: np.ndarray) -> np.ndarray:

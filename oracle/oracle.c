@@ -27,7 +27,10 @@
  *   orc_maxgrid     scipy.ndimage.maximum_filter on random levels
  *   orc_render      Beer-Lambert slab closed form, axis-aligned views against a
  *                   product-form compositor over scipy map_coordinates samples,
- *                   empty volume, axis-aligned sample counts
+ *                   empty volume, axis-aligned sample counts; oblique views:
+ *                   camera bases against hand-derived vectors and frame
+ *                   properties, sample counts against FP64 ray-box chords,
+ *                   renders against the product form over FP64 positions
  *   orc_hough_circle      drawn rings of known centre and radius, the phantom
  *                         container's axis and inner radius, an image without
  *                         edges
@@ -36,8 +39,11 @@
  *                         luminance weights, counts sum to the pixel count
  *   orc_render_dense      orc_render on the same level (intensities = raw/255),
  *                         Beer-Lambert slab
+ *   orc_render_dense_band its three results equal orc_render_dense stopped at
+ *                         alpha_stop - eps, alpha_stop, alpha_stop + eps
  *   orc_render_dense_grad central finite differences of orc_render_dense along
- *                         random directions; closed-form dA/dalpha of a slab
+ *                         random directions; closed-form dA/dalpha of a slab;
+ *                         term magnitudes bound |gradient|, scale with it
  * No function here is "parity unpinned".
  */
 #include <math.h>
@@ -699,6 +705,88 @@ static int dense_args_ok(const double *vol, int64_t mx, int64_t my, int64_t mz, 
     return 1;
 }
 
+/* One ray of the dense render, marched until its opacity reaches the highest
+ * of the three stop levels stops[0] <= stops[1] <= stops[2]; out[s] and cnt[s]
+ * hold (C, A) and the number of samples at the first sample where A >= stops[s]
+ * (the last sample when A never gets there). */
+static void dense_ray(const double *vol, const int64_t M[3], const double Nd[3], const double *lut, int nlut,
+                      const orc_ray *ray, const double stops[3], double out[3][4], uint64_t cnt[3])
+{
+    double C[3] = {0, 0, 0}, A = 0.0;
+    int done[3] = {0, 0, 0};
+    int64_t k = 0;
+    while (k < ray->n && !done[2]) {
+        double t = (double)ray->t_near + ((double)k + 0.5) * (double)ray->delta;
+        double q[3];
+        for (int a = 0; a < 3; ++a) q[a] = (((double)ray->o[a] + t * (double)ray->d[a]) * (double)M[a]) / Nd[a] - 0.5;
+        orc_tap tp;
+        dense_tap(vol, M, q, &tp);
+        double v = tp.raw < 0.0 ? 0.0 : (tp.raw > 1.0 ? 1.0 : tp.raw);
+        double e[4];
+        int64_t j;
+        double f;
+        dense_lookup(lut, nlut, v, e, &j, &f);
+        double w = (1.0 - A) * e[3];
+        C[0] += w * e[0];
+        C[1] += w * e[1];
+        C[2] += w * e[2];
+        A += w;
+        ++k;
+        for (int s2 = 0; s2 < 3; ++s2) {
+            if (!done[s2] && A >= stops[s2]) {
+                done[s2] = 1;
+                out[s2][0] = C[0]; out[s2][1] = C[1]; out[s2][2] = C[2]; out[s2][3] = A;
+                cnt[s2] = (uint64_t)k;
+            }
+        }
+    }
+    for (int s2 = 0; s2 < 3; ++s2) {
+        if (!done[s2]) {
+            out[s2][0] = C[0]; out[s2][1] = C[1]; out[s2][2] = C[2]; out[s2][3] = A;
+            cnt[s2] = (uint64_t)k;
+        }
+    }
+}
+
+/*
+ * The dense render with the early-exit band of orc_render: rgba (stop at
+ * alpha_stop), rgba_lo (at alpha_stop - eps) and rgba_hi (at alpha_stop + eps),
+ * nsamp[p][3] the three sample counts; rgba_lo, rgba_hi and nsamp may be NULL.
+ * A ray whose lo and hi results differ may stop anywhere between them in an
+ * FP32 march (several results are correct).
+ */
+int orc_render_dense_band(const double *vol, int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny,
+                          int64_t nz, const double *lut, int nlut, double alpha_stop, double eps,
+                          const orc_view *view, const int64_t *pixels, int64_t npix, double *rgba,
+                          double *rgba_lo, double *rgba_hi, uint64_t *nsamp)
+{
+    if (!dense_args_ok(vol, mx, my, mz, nx, ny, nz, lut, nlut, view) || !rgba || !(eps >= 0.0)) return ORC_EINVAL;
+    orc_cam cam;
+    dense_camera(mx, my, mz, nx, ny, nz, view, &cam);
+    const int64_t M[3] = {mx, my, mz};
+    const double Nd[3] = {(double)nx, (double)ny, (double)nz};
+    const double stops[3] = {alpha_stop - eps, alpha_stop, alpha_stop + eps};
+    const int64_t W = view->width, H = view->height;
+    const int64_t total = pixels ? npix : W * H;
+    for (int64_t p = 0; p < total; ++p) {
+        int64_t lin = pixels ? pixels[p] : p;
+        if (lin < 0 || lin >= W * H) return ORC_EINVAL;
+        orc_ray ray;
+        ray_setup(cam.bf, cam.rf, cam.uf, cam.L, cam.c, cam.N, cam.delta, view->width, view->height, lin % W,
+                  lin / W, &ray);
+        double out[3][4];
+        uint64_t cnt[3];
+        dense_ray(vol, M, Nd, lut, nlut, &ray, stops, out, cnt);
+        for (int ch = 0; ch < 4; ++ch) {
+            rgba[p * 4 + ch] = out[1][ch];
+            if (rgba_lo) rgba_lo[p * 4 + ch] = out[0][ch];
+            if (rgba_hi) rgba_hi[p * 4 + ch] = out[2][ch];
+        }
+        if (nsamp) { nsamp[p * 3 + 0] = cnt[0]; nsamp[p * 3 + 1] = cnt[1]; nsamp[p * 3 + 2] = cnt[2]; }
+    }
+    return ORC_OK;
+}
+
 int orc_render_dense(const double *vol, int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny, int64_t nz,
                      const double *lut, int nlut, double alpha_stop, const orc_view *view,
                      const int64_t *pixels, int64_t npix, double *rgba, uint64_t *nsamp)
@@ -708,6 +796,7 @@ int orc_render_dense(const double *vol, int64_t mx, int64_t my, int64_t mz, int6
     dense_camera(mx, my, mz, nx, ny, nz, view, &cam);
     const int64_t M[3] = {mx, my, mz};
     const double Nd[3] = {(double)nx, (double)ny, (double)nz};
+    const double stops[3] = {alpha_stop, alpha_stop, alpha_stop};
     const int64_t W = view->width, H = view->height;
     const int64_t total = pixels ? npix : W * H;
     for (int64_t p = 0; p < total; ++p) {
@@ -716,32 +805,11 @@ int orc_render_dense(const double *vol, int64_t mx, int64_t my, int64_t mz, int6
         orc_ray ray;
         ray_setup(cam.bf, cam.rf, cam.uf, cam.L, cam.c, cam.N, cam.delta, view->width, view->height, lin % W,
                   lin / W, &ray);
-        double C[3] = {0, 0, 0}, A = 0.0;
-        int64_t k = 0;
-        while (k < ray.n) {
-            double t = (double)ray.t_near + ((double)k + 0.5) * (double)ray.delta;
-            double q[3];
-            for (int a = 0; a < 3; ++a) q[a] = (((double)ray.o[a] + t * (double)ray.d[a]) * (double)M[a]) / Nd[a] - 0.5;
-            orc_tap tp;
-            dense_tap(vol, M, q, &tp);
-            double v = tp.raw < 0.0 ? 0.0 : (tp.raw > 1.0 ? 1.0 : tp.raw);
-            double e[4];
-            int64_t j;
-            double f;
-            dense_lookup(lut, nlut, v, e, &j, &f);
-            double w = (1.0 - A) * e[3];
-            C[0] += w * e[0];
-            C[1] += w * e[1];
-            C[2] += w * e[2];
-            A += w;
-            ++k;
-            if (A >= alpha_stop) break;
-        }
-        rgba[p * 4 + 0] = C[0];
-        rgba[p * 4 + 1] = C[1];
-        rgba[p * 4 + 2] = C[2];
-        rgba[p * 4 + 3] = A;
-        if (nsamp) nsamp[p] = (uint64_t)k;
+        double out[3][4];
+        uint64_t cnt[3];
+        dense_ray(vol, M, Nd, lut, nlut, &ray, stops, out, cnt);
+        for (int ch = 0; ch < 4; ++ch) rgba[p * 4 + ch] = out[1][ch];
+        if (nsamp) nsamp[p] = cnt[1];
     }
     return ORC_OK;
 }
@@ -758,10 +826,14 @@ int orc_render_dense(const double *vol, int64_t mx, int64_t my, int64_t mz, int6
  * Then the lookup: g lut[j] += (1-f) g e, g lut[j+1] += f g e, and
  * g v = (nlut-1) sum_ch g e_ch (lut[j+1]_ch - lut[j]_ch) inside 0 < raw < 1
  * (0 where the clamp is active); g vol[corner] += w_corner g v.
+ * g_vol_mag / g_lut_mag (may be NULL) receive, per element, the sum of the
+ * absolute values of the terms added into it: the scale against which the
+ * rounding error of any order of summing those terms is measured.
  */
 int orc_render_dense_grad(const double *vol, int64_t mx, int64_t my, int64_t mz, int64_t nx, int64_t ny,
                           int64_t nz, const double *lut, int nlut, double alpha_stop, const orc_view *view,
-                          const double *g_rgba, double *g_vol, double *g_lut)
+                          const double *g_rgba, double *g_vol, double *g_lut, double *g_vol_mag,
+                          double *g_lut_mag)
 {
     if (!dense_args_ok(vol, mx, my, mz, nx, ny, nz, lut, nlut, view) || !g_rgba || !g_vol || !g_lut)
         return ORC_EINVAL;
@@ -819,11 +891,18 @@ int orc_render_dense_grad(const double *vol, int64_t mx, int64_t my, int64_t mz,
             for (int ch = 0; ch < 4; ++ch) {
                 g_lut[j * 4 + ch] += (1.0 - f) * ge[ch];
                 g_lut[(j + 1) * 4 + ch] += f * ge[ch];
+                if (g_lut_mag) {
+                    g_lut_mag[j * 4 + ch] += fabs((1.0 - f) * ge[ch]);
+                    g_lut_mag[(j + 1) * 4 + ch] += fabs(f * ge[ch]);
+                }
                 gv += ge[ch] * (lut[(j + 1) * 4 + ch] - lut[j * 4 + ch]);
             }
             gv *= (double)(nlut - 1);
             if (!(taps[k].raw > 0.0 && taps[k].raw < 1.0)) gv = 0.0;
-            for (int c = 0; c < 8; ++c) g_vol[taps[k].idx[c]] += taps[k].w[c] * gv;
+            for (int c = 0; c < 8; ++c) {
+                g_vol[taps[k].idx[c]] += taps[k].w[c] * gv;
+                if (g_vol_mag) g_vol_mag[taps[k].idx[c]] += fabs(taps[k].w[c] * gv);
+            }
         }
     }
     free(taps); free(Ak); free(E); free(F); free(J);

@@ -80,3 +80,44 @@ def test_dense_grad_zero_where_clamped(orc):
     gv, gl = orc.render_dense_grad(vol, (10, 10, 10), lut, 10.0, 5.0, 6, 6, g, 0.5, 1.0)
     assert np.all(gv == 0.0)
     assert np.any(gl[-1] != 0.0)
+
+
+def test_dense_band_edges_are_plain_renders(orc):
+    """The band's lo / mid / hi results are the plain dense render stopped at
+    alpha_stop - eps, alpha_stop and alpha_stop + eps (the early-exit straddle
+    reading), with ordered sample counts."""
+    rng = np.random.default_rng(21)
+    vol = rng.uniform(0.05, 0.95, (9, 8, 10))
+    lut = rng.uniform(0.0, 1.0, (16, 4))
+    lut[:, 3] *= 0.4
+    src, view, stop, eps = (30, 24, 27), (41.0, -23.0, 12, 10, 0.5), 0.95, 0.02
+    band = orc.render_dense_band(vol, src, lut, *view, stop, eps)
+    for key, level, col in (("lo", stop - eps, 0), ("rgba", stop, 1), ("hi", stop + eps, 2)):
+        r, ns = orc.render_dense(vol, src, lut, *view, level)
+        assert np.array_equal(band[key], r)
+        assert np.array_equal(band["nsamp"][..., col], ns)
+    ns = band["nsamp"].astype(np.int64)
+    assert np.all(ns[..., 0] <= ns[..., 1]) and np.all(ns[..., 1] <= ns[..., 2])
+    assert np.any(ns[..., 0] < ns[..., 2])
+    flat = orc.render_dense_band(vol, src, lut, *view, stop, 0.0)
+    assert np.array_equal(flat["lo"], flat["rgba"]) and np.array_equal(flat["hi"], flat["rgba"])
+
+
+def test_dense_grad_magnitudes(orc):
+    """The per-element magnitude is the sum of |terms|: it bounds |gradient|,
+    is unchanged when the upstream gradient changes sign (the gradient flips),
+    and scales with it."""
+    rng = np.random.default_rng(22)
+    vol = rng.uniform(0.05, 0.95, (6, 7, 8))
+    lut = rng.uniform(0.0, 1.0, (8, 4))
+    lut[:, 3] *= 0.3
+    src, view = (16, 14, 12), (25.0, 10.0, 9, 7)
+    g = rng.normal(size=(7, 9, 4))
+    gv, gl, mv, ml = orc.render_dense_grad(vol, src, lut, *view, g, 0.5, 0.99, magnitudes=True)
+    assert np.all(mv >= np.abs(gv) * (1 - 1e-12)) and np.all(ml >= np.abs(gl) * (1 - 1e-12))
+    assert np.any(mv > np.abs(gv) * 1.01)          # terms of both signs meet in some voxels
+    gv2, gl2, mv2, ml2 = orc.render_dense_grad(vol, src, lut, *view, -2.0 * g, 0.5, 0.99, magnitudes=True)
+    assert np.allclose(gv2, -2.0 * gv, rtol=1e-12, atol=1e-15) and np.allclose(mv2, 2.0 * mv, rtol=1e-12, atol=1e-15)
+    assert np.allclose(gl2, -2.0 * gl, rtol=1e-12, atol=1e-15) and np.allclose(ml2, 2.0 * ml, rtol=1e-12, atol=1e-15)
+    gv3, gl3 = orc.render_dense_grad(vol, src, lut, *view, g, 0.5, 0.99)
+    assert np.array_equal(gv3, gv) and np.array_equal(gl3, gl)
