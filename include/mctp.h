@@ -324,8 +324,13 @@ int mctp_render_batch(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
  *   MCTP_BATCH_STATIC_SCRATCH bytes is rejected with MCTP_ESIZE before
  *   anything is enqueued.
  *   The first call with a device current looks up the scratch address on
- *   that device (a host-side query, no allocation); make that first call
- *   before any stream capture.
+ *   that device; make that first call before any stream capture.  The lookup
+ *   allocates nothing itself, but CUDA loads a library's device code lazily:
+ *   if no kernel of this library has run on the device yet, the lookup loads
+ *   it, and loading places the code and the scratch array in device memory
+ *   (as the first launch of any kernel would).  The address is kept for the
+ *   life of the process; after cudaDeviceReset the library must be unloaded
+ *   and loaded again before this call is used.
  *   Nothing in the scratch needs to start at zero: every call rewrites what
  *   it uses (the work counter is cleared by an in-stream memset).
  *   All calls on one device share the one scratch: two calls whose work can

@@ -44,6 +44,23 @@ def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+def _out(t: torch.Tensor, name: str, dtype: torch.dtype, numel: int, device) -> torch.Tensor:
+    """Check a caller-supplied output buffer before its pointer reaches the
+    library, which cannot see its size: a contiguous CUDA tensor of `dtype`
+    with at least `numel` elements on `device`."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, {numel} needed")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if device is not None and t.device != torch.device(device):
+        raise ValueError(f"{name} is on {t.device}, the inputs on {device}")
+    return t
+
+
 def volume_desc(vol: torch.Tensor, bits: int) -> _lib.VolumeDesc:
     if vol.dim() != 3 or vol.dtype not in _DTYPES:
         raise ValueError("volume must be a 3-D uint8/uint16 tensor [nz][ny][nx]")
@@ -75,6 +92,8 @@ def build_histogram(vol: torch.Tensor, bits: int, nbins: int, z0: int = 0, z1: i
         hist = torch.empty(nbins, dtype=torch.uint64, device=vol.device)
     if overflow is None:
         overflow = torch.empty(1, dtype=torch.uint64, device=vol.device)
+    _out(hist, "hist", torch.uint64, nbins, vol.device)
+    _out(overflow, "overflow", torch.uint64, 1, vol.device)
     _lib.check(_lib.load().mctp_build_histogram(_ptr(vol), ctypes.byref(d), z0, z1, nbins, _ptr(hist),
                                                 _ptr(overflow), _stream(stream)), "mctp_build_histogram")
     return hist, overflow
@@ -96,6 +115,8 @@ def select_threshold(hist: torch.Tensor | None, nbins: int | None = None, mode: 
         keep = torch.empty(nbins, dtype=torch.uint8, device=device)
     if result is None:
         result = torch.empty(4, dtype=torch.int32, device=device)
+    _out(keep, "keep", torch.uint8, nbins, device)
+    _out(result, "result", torch.int32, 4, device)
     _lib.check(_lib.load().mctp_select_threshold(_ptr(hist), nbins, ctypes.byref(p), _ptr(keep), _ptr(result),
                                                  _stream(stream)), "mctp_select_threshold")
     return keep, result
@@ -109,6 +130,7 @@ def filter_threshold(vol: torch.Tensor, bits: int, keep: torch.Tensor, out: torc
     d = volume_desc(vol, bits)
     if out is None:
         out = torch.empty_like(vol)
+    _out(out, "out", vol.dtype, vol.numel(), vol.device)
     _lib.check(_lib.load().mctp_filter_threshold(_ptr(vol), ctypes.byref(d), _ptr(keep), keep.numel(), _ptr(out),
                                                  _stream(stream)), "mctp_filter_threshold")
     return out
@@ -266,6 +288,8 @@ def render_views(sm: Slicemap, views, lut: torch.Tensor, alpha_stop: float = 0.9
         out = torch.empty(max(total, 4), dtype=torch.float32, device=dev)
     if samples is None:
         samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    _out(out, "out", torch.float32, total, dev)
+    _out(samples, "samples", torch.uint64, 1, dev)
     s = sm.desc()
     arr = view_array(views)
     _lib.check(_lib.load().mctp_render_views(ctypes.byref(s), arr, len(views), _ptr(lut), lut.shape[0],
@@ -348,12 +372,14 @@ def render_batch(slicemaps, views, view_slicemap, view_lut, luts: torch.Tensor, 
                                                ctypes.byref(nb)), "mctp_render_batch_workspace")
     if workspace is None:
         workspace = torch.empty(nb.value, dtype=torch.uint8, device=dev)
-    _cuda(workspace, "workspace")
+    _out(workspace, "workspace", torch.uint8, nb.value, dev)
     total = sum(v.width * v.height * 4 for v in views)
     if out is None:
         out = torch.empty(max(total, 4), dtype=torch.float32, device=dev)
     if samples is None:
         samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    _out(out, "out", torch.float32, total, dev)
+    _out(samples, "samples", torch.uint64, 1, dev)
     t = (tuning or BatchTuning()).c()
     _lib.check(lib.mctp_render_batch(a.sms, a.nsm, a.views, a.vsm, a.vlut, a.n, _ptr(luts), luts.shape[0],
                                      luts.shape[1], alpha_stop, ctypes.byref(t), _ptr(out), _ptr(samples),
@@ -382,6 +408,8 @@ def render_batch_static(slicemaps, views, view_slicemap, view_lut, luts: torch.T
         out = torch.empty(max(total, 4), dtype=torch.float32, device=dev)
     if samples is None:
         samples = torch.empty(1, dtype=torch.uint64, device=dev)
+    _out(out, "out", torch.float32, total, dev)
+    _out(samples, "samples", torch.uint64, 1, dev)
     t = (tuning or BatchTuning()).c()
     _lib.check(_lib.load().mctp_render_batch_static(a.sms, a.nsm, a.views, a.vsm, a.vlut, a.n, _ptr(luts),
                                                     luts.shape[0], luts.shape[1], alpha_stop, ctypes.byref(t),
@@ -396,12 +424,16 @@ def image_entropy(flat: torch.Tensor, views, hist: torch.Tensor | None = None, e
     _cuda(flat, "images")
     dev = flat.device
     n = len(views)
+    _out(flat, "images", torch.float32, sum(v.width * v.height * 4 for v in views), dev)
     if hist is None:
         hist = torch.empty((max(n, 1), 256), dtype=torch.uint64, device=dev)
     if entropy is None:
         entropy = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
     if best is None:
         best = torch.empty(1, dtype=torch.int32, device=dev)
+    _out(hist, "hist", torch.uint64, n * 256, dev)
+    _out(entropy, "entropy", torch.float64, n, dev)
+    _out(best, "best", torch.int32, 1, dev)
     _lib.check(_lib.load().mctp_image_entropy(_ptr(flat), view_array(views), n, _ptr(hist), _ptr(entropy), _ptr(best),
                                               _stream(stream)), "mctp_image_entropy")
     return hist, entropy, best
@@ -438,6 +470,7 @@ def mask_container(vol: torch.Tensor, bits: int, circle: torch.Tensor, margin: i
     d = volume_desc(vol, bits)
     if out is None:
         out = torch.empty_like(vol)
+    _out(out, "out", vol.dtype, vol.numel(), vol.device)
     _lib.check(_lib.load().mctp_mask_container(_ptr(vol), ctypes.byref(d), _ptr(circle), margin, _ptr(out),
                                                _stream(stream)), "mctp_mask_container")
     return out

@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(kHistThreads)
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-        uint32_t sum = 0;
+        unsigned long long sum = 0;  // 32 columns of up to 2^31 each
         for (int l = 0; l < 32; ++l) sum += sh_cols[b * 32 + ((l + b) & 31)];  // rotated: no bank conflicts
-        if (sum) atomicAdd(&hist[b], (unsigned long long)sum);
+        if (sum) atomicAdd(&hist[b], sum);
     }
     if (kCheckOverflow) {
 #pragma unroll

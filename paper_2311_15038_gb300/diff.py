@@ -10,7 +10,7 @@ import ctypes
 
 import torch
 
-from . import _cuda, _lib, _ptr, _stream, view_array
+from . import _cuda, _lib, _out, _ptr, _stream, view_array
 
 
 def _dims(vol: torch.Tensor):
@@ -42,6 +42,8 @@ def render_dense(vol: torch.Tensor, lut: torch.Tensor, views, src_dims, alpha_st
         out = torch.empty(max(total, 4), dtype=torch.float32, device=vol.device)
     if samples is None:
         samples = torch.empty(1, dtype=torch.uint64, device=vol.device)
+    _out(out, "out", torch.float32, total, vol.device)
+    _out(samples, "samples", torch.uint64, 1, vol.device)
     _lib.check(_lib.load().mctp_render_dense(_ptr(vol), mx, my, mz, _src(src_dims), view_array(views), len(views),
                                              _ptr(lut), lut.shape[0], alpha_stop, _ptr(out), _ptr(samples),
                                              _stream(stream)), "mctp_render_dense")
@@ -54,11 +56,13 @@ def render_dense_backward(vol: torch.Tensor, lut: torch.Tensor, views, src_dims,
     """(dL/dvol, dL/dlut) given dL/d(images) (the flat buffer of render_dense)."""
     mx, my, mz = _dims(vol)
     _lut(lut)
-    _cuda(grad_rgba, "grad_rgba")
+    _out(grad_rgba, "grad_rgba", torch.float32, sum(v.width * v.height * 4 for v in views), vol.device)
     if grad_vol is None:
         grad_vol = torch.empty_like(vol)
     if grad_lut is None:
         grad_lut = torch.empty_like(lut)
+    _out(grad_vol, "grad_vol", torch.float32, vol.numel(), vol.device)
+    _out(grad_lut, "grad_lut", torch.float32, lut.numel(), vol.device)
     _lib.check(_lib.load().mctp_render_dense_backward(_ptr(vol), mx, my, mz, _src(src_dims), view_array(views),
                                                       len(views), _ptr(lut), lut.shape[0], alpha_stop,
                                                       _ptr(grad_rgba), _ptr(grad_vol), _ptr(grad_lut),
@@ -88,9 +92,12 @@ def l2_loss(x: torch.Tensor, target: torch.Tensor, scale: float = 1.0, grad: tor
             loss: torch.Tensor | None = None, stream=None):
     """(loss float32[1] = scale sum (x - t)^2, grad = 2 scale (x - t))."""
     _cuda(x, "x")
-    _cuda(target, "target")
+    _out(target, "target", x.dtype, x.numel(), x.device)
     if loss is None:
         loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _out(loss, "loss", torch.float32, 1, x.device)
+    if grad is not None:
+        _out(grad, "grad", torch.float32, x.numel(), x.device)
     _lib.check(_lib.load().mctp_l2_loss(_ptr(x), _ptr(target), x.numel(), scale, _ptr(grad), _ptr(loss),
                                         _stream(stream)), "mctp_l2_loss")
     return loss, grad
@@ -99,6 +106,9 @@ def l2_loss(x: torch.Tensor, target: torch.Tensor, scale: float = 1.0, grad: tor
 def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int, lr: float,
               beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, lo: float = -3.4e38, hi: float = 3.4e38,
               stream=None) -> None:
+    _cuda(param, "param")
+    for t, name in ((grad, "grad"), (m, "m"), (v, "v")):
+        _out(t, name, param.dtype, param.numel(), param.device)
     _lib.check(_lib.load().mctp_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2,
                                           eps, step, lo, hi, _stream(stream)), "mctp_adam_step")
 

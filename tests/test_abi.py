@@ -343,3 +343,20 @@ def test_atlas_texture_rejects(lib):
     assert lib.mctp_atlas_texture_create(ctypes.byref(bad), 0, ctypes.byref(out), ctypes.byref(h)) == -3
     assert lib.mctp_atlas_texture_update(None, ctypes.byref(s), 0, None) == -1
     assert lib.mctp_atlas_texture_destroy(None) == 0
+
+
+def test_binding_refuses_short_or_mistyped_outputs():
+    """The library cannot see the size of a buffer behind a pointer, so the
+    binding checks every caller-supplied output before the call: a buffer too
+    small for the batch (the kernel would write past its end), of the wrong
+    element type, or not on a CUDA device is refused with ValueError."""
+    import torch
+    import paper_2311_15038_gb300 as mctp
+    with pytest.raises(ValueError, match="elements"):
+        mctp._out(torch.empty(3, dtype=torch.float32), "out", torch.float32, 16, None)
+    with pytest.raises(ValueError, match="float32"):
+        mctp._out(torch.empty(64, dtype=torch.float64), "out", torch.float32, 16, None)
+    with pytest.raises(ValueError, match="uint64"):
+        mctp._out(torch.empty(1, dtype=torch.int64), "samples", torch.uint64, 1, None)
+    with pytest.raises(ValueError, match="CUDA"):
+        mctp._out(torch.empty(64, dtype=torch.float32), "out", torch.float32, 16, None)

@@ -291,3 +291,31 @@ def test_depth_bounds_edge_cases(env):
     sm.update_textures()
     flat, smp, _ = mctp.render_batch([sm], views, vsm, vlut, luts, 0.99)
     assert torch.equal(flat[:ref.numel()], ref) and int(smp.item()) == ref_s
+
+
+def test_binding_refuses_short_outputs_on_the_device(env):
+    """A caller-supplied image buffer one element short, a sample counter of
+    the wrong type or a workspace too small is refused before the launch, in
+    both batched entry points (the kernels would write past its end)."""
+    mctp, oracle, phantom, dev = env
+    sms = _slicemaps(env, [(phantom.VolumeSpec(40, 36, 32, bits=8, seed=9, n_ell=3), [(20, 18, 16)], True)])
+    views = [mctp.View(20.0, 10.0, 16, 12, 0, 0.5), mctp.View(-40.0, 5.0, 9, 7, 0, 0.5)]
+    luts = up(_luts(phantom), dev)
+    total = sum(v.width * v.height * 4 for v in views)
+    short = torch.empty(total - 1, dtype=torch.float32, device=dev)
+    with pytest.raises(ValueError, match="elements"):
+        mctp.render_batch([sms[0][1]], views, [0, 0], [0, 1], luts, out=short)
+    with pytest.raises(ValueError, match="elements"):
+        mctp.render_batch_static([sms[0][1]], views, [0, 0], [0, 1], luts, out=short)
+    with pytest.raises(ValueError, match="uint64"):
+        mctp.render_batch_static([sms[0][1]], views, [0, 0], [0, 1], luts,
+                                 samples=torch.empty(1, dtype=torch.int64, device=dev))
+    with pytest.raises(ValueError, match="elements"):
+        mctp.render_batch([sms[0][1]], views, [0, 0], [0, 1], luts,
+                          workspace=torch.empty(64, dtype=torch.uint8, device=dev))
+    # the exact size is accepted and renders what render_views renders
+    exact = torch.empty(total, dtype=torch.float32, device=dev)
+    out, samples = mctp.render_batch_static([sms[0][1]], views, [0, 0], [0, 1], luts, out=exact)
+    ref0, _ = mctp.render_views(sms[0][1], views[:1], luts[0])
+    torch.cuda.synchronize()
+    assert torch.equal(out[:ref0.numel()], ref0[:16 * 12 * 4])
