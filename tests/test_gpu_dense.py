@@ -161,7 +161,10 @@ def test_dense_adjoint_across_checkpoints(env, name, stop):
                                         g_flat, stop)
     gv = gv.cpu().numpy().astype(np.float64)
     gl = gl.cpu().numpy().astype(np.float64)
-    tol_rel = 2e-3
+    # The FP32 transmittance after k samples carries a relative error of about k
+    # roundings (k <= 2048 here), and each term's error is relative to the term:
+    # 4 * 2048 * 2^-24 = 4.9e-4 of the sum of |terms| bounds any summation order.
+    tol_rel = 4 * 2048 * 2.0 ** -24
     for what, got, ref, mag in (("volume", gv, rv, mv), ("LUT", gl, rl, ml)):
         err = np.abs(got - ref)
         scale = np.maximum(mag, 1e-30)
@@ -229,7 +232,7 @@ def test_dense_adjoint_straddling_rays(env, name):
             best = min(best, r)
         print(f"{name}: straddling ray ({i}, {j}) samples {ns[j, i, 0]}..{ns[j, i, 2]}: "
               f"closest allowed stop max |err|/sum|terms| = {best:.2e}")
-        assert best <= 2e-3
+        assert best <= 4 * 2048 * 2.0 ** -24
 
 
 def test_dense_gradient_central_differences(env):
