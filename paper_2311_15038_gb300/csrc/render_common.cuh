@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "mctp_internal.cuh"
 
@@ -216,6 +217,251 @@ struct DepthRange {
     uint32_t lo, hi;
 };
 
+// FP32 set-up of one ray: origin, direction, entry distance and sample count.
+struct RaySpan {
+    float o[3], d[3];
+    float tmin;
+    int n;  // samples of the ray; 0 when it misses the box
+};
+
+// The ray of pixel (px, py) of view V, one rounding per operation in a fixed
+// order (camera origin, slab intersection, n = floor((t_far - t_near) / Delta)).
+__device__ __forceinline__ RaySpan ray_span(const ViewParams &V, int px, int py)
+{
+    RaySpan R;
+    const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
+    const float sy = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn(float(py), 0.5f), float(V.H)));
+    const float sxL = __fmul_rn(sx, V.L), syL = __fmul_rn(sy, V.L);
+    float tmin = -INFINITY, tmax = INFINITY;
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float t1 = __fadd_rn(V.c[a], __fmul_rn(sxL, V.r[a]));
+        const float t2 = __fadd_rn(t1, __fmul_rn(syL, V.u[a]));
+        R.o[a] = __fadd_rn(t2, __fmul_rn(V.L, V.b[a]));
+        R.d[a] = -V.b[a];
+        if (R.d[a] != 0.0f) {
+            const float inv = V.inv_d[a];  // = __frcp_rn(d[a]), rounded once on the host
+            const float s0 = __fmul_rn(__fsub_rn(0.0f, R.o[a]), inv);
+            const float s1 = __fmul_rn(__fsub_rn(V.N[a], R.o[a]), inv);
+            tmin = fmaxf(tmin, fminf(s0, s1));
+            tmax = fminf(tmax, fmaxf(s0, s1));
+        } else if (!(R.o[a] >= 0.0f && R.o[a] <= V.N[a])) {
+            miss = true;
+        }
+    }
+    R.tmin = tmin;
+    R.n = 0;
+    if (!miss && tmax > tmin) R.n = int(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
+    if (R.n < 0) R.n = 0;
+    return R;
+}
+
+// Samples [k0, kend) of a ray of n > 0 samples that can reach a marked cell;
+// the others have opacity exactly 0.  Sample k sits at depth
+// tmin + (k + 1/2) Delta - L, so k = (depth + L - tmin) / Delta - 1/2; two
+// samples of margin cover the rounding of this estimate (the raster already
+// adds a voxel).  False when the ray meets no marked cell at all.
+__device__ __forceinline__ bool ray_range(const ViewParams &V, const RaySpan &R, DepthRange range, int &k0,
+                                          int &kend)
+{
+    k0 = 0;
+    kend = R.n;
+    if (!range.on) return true;
+    if (range.lo > range.hi) return false;
+    const float inv_d = 1.0f / V.delta;
+    const float klo = (__uint_as_float(range.lo) - R.tmin) * inv_d - 2.5f;
+    const float khi = (__uint_as_float(range.hi) - R.tmin) * inv_d + 2.5f;
+    k0 = int(fminf(fmaxf(klo, 0.0f), float(R.n)));
+    kend = int(fminf(fmaxf(khi, 0.0f), float(R.n - 1))) + 1;
+    return true;
+}
+
+// Fixed-point level coordinates of sample k of the ray.
+__device__ __forceinline__ void ray_coords(const ViewParams &V, const RaySpan &R, int k, long long U[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        U[a] = start_coord(R.o[a], R.d[a], R.tmin, 0.5f * V.delta, V.sc_hi[a], V.sc_lo[a]) + (long long)k * V.dU[a];
+}
+
+// March state of one ray from its first sample that can reach a marked cell
+// to its end: the fixed-point coordinates U of sample k; the exact integer
+// DDA over the 8^3 cells of each sample's lower corner (cc: current cell;
+// nxt[a]: the first sample index whose corner is in the next cell along axis
+// a, past the ray's end for none; ee: the slack of that crossing; kmin: the
+// least nxt); the compositing sums; the current slice pair's atlas offsets.
+struct RayMarch {
+    long long U[3];
+    int k, kend, n;
+    int cc[3], nxt[3];
+    uint32_t ee[3];
+    int kmin;
+    bool occupied;
+    float C0, C1, C2, A;
+    int zc;               // level slice of the cached offsets (INT_MIN: none)
+    uint32_t za, zb;      // texel offsets (or texture origins) of slices zc and zc + 1, clamped
+    int nev;              // samples evaluated (counted only with kCount)
+};
+
+// Cell bit of cc in the bitmap.
+template <class Tab>
+__device__ __forceinline__ bool cell_marked(const Tab &tab, const LevelGeom &G, const int cc[3])
+{
+    const uint32_t word = tab.occ_at((cc[2] * G.gy + cc[1]) * G.wpr + (cc[0] >> 5));
+    return (word >> (cc[0] & 31)) & 1u;
+}
+
+// State at sample k0 given that sample's coordinates U; with the DDA when
+// `skip` (empty cells are jumped over), else every cell counts as marked.
+// With m = |dU| (< 2^32) and D = 8 voxels = q m + r, the crossing after one
+// at c (slack e = c m - distance, 0 <= e < m) is at c + q + (r > e), slack
+// e + (r > e ? m : 0) - r.
+template <class Tab>
+__device__ __forceinline__ void march_begin(RayMarch &S, const ViewParams &V, const LevelGeom &G, bool skip,
+                                            const Tab &tab, const long long U[3], int k0, int kend, int n)
+{
+    constexpr int kInf = 0x7fffffff;
+    S.k = k0;
+    S.kend = kend;
+    S.n = n;
+    S.C0 = S.C1 = S.C2 = S.A = 0.f;
+    S.zc = INT_MIN;
+    S.za = S.zb = 0u;
+    S.nev = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        S.U[a] = U[a];
+        S.cc[a] = min(max(int(U[a] >> 32), 0), G.m1[a]) >> 3;  // cell of sample k0
+        S.nxt[a] = kInf;
+        S.ee[a] = 0;
+        const long long dU = V.dU[a];
+        const int last = G.m1[a] >> 3;
+        if (skip && dU != 0 && (dU > 0 ? S.cc[a] < last : S.cc[a] > 0)) {
+            const long long U0 = U[a] - (long long)k0 * dU;  // coordinates of sample 0
+            const long long m = dU > 0 ? dU : -dU;
+            const long long num = dU > 0 ? ((long long)(8 * S.cc[a] + 8) << 32) - U0
+                                         : U0 - ((long long)(8 * S.cc[a]) << 32) + 1;
+            // c = ceil(num / m): float estimate, then exact correction
+            const float est = float(num) * V.inv_m[a];
+            if (est < float(n) + 2.0f) {
+                long long c = (long long)est;
+                while (c * m < num) ++c;
+                while (c > 0 && (c - 1) * m >= num) --c;
+                S.nxt[a] = int(c);
+                S.ee[a] = uint32_t(c * m - num);
+            }
+        }
+    }
+    S.kmin = min(min(S.nxt[0], S.nxt[1]), S.nxt[2]);
+    S.occupied = skip ? cell_marked(tab, G, S.cc) : true;
+}
+
+// The DDA crosses into the next cell along every axis whose crossing is at
+// sample k (= kmin), and refreshes the current cell's bit.
+template <class Tab>
+__device__ __forceinline__ void march_cross(RayMarch &S, const ViewParams &V, const LevelGeom &G, const Tab &tab)
+{
+    constexpr int kInf = 0x7fffffff;
+    const int k = S.kmin;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (S.nxt[a] != k) continue;
+        const bool fwd = V.dU[a] > 0;
+        S.cc[a] += fwd ? 1 : -1;
+        if (fwd ? S.cc[a] >= (G.m1[a] >> 3) : S.cc[a] <= 0) {
+            S.nxt[a] = kInf;  // the last cell this way: clamping keeps the corner in it
+            continue;
+        }
+        const uint32_t m = uint32_t(fwd ? V.dU[a] : -V.dU[a]);
+        const bool up = V.rr[a] > S.ee[a];
+        S.nxt[a] = int(min(uint32_t(S.nxt[a]) + V.qq[a] + (up ? 1u : 0u), uint32_t(kInf)));
+        S.ee[a] += (up ? m : 0u) - V.rr[a];
+    }
+    S.kmin = min(min(S.nxt[0], S.nxt[1]), S.nxt[2]);
+    S.occupied = cell_marked(tab, G, S.cc);
+}
+
+// One iteration of the march: a jump over an empty cell, or one sample
+// (trilinear interpolation, transfer function, compositing).  Returns true
+// when the ray is finished: past its last sample that can reach a marked
+// cell, or stopped early once A >= alpha_stop.
+template <typename T, bool kCount, class Tab>
+__device__ __forceinline__ bool march_step(RayMarch &S, const ViewParams &V, const T *atlas, const LevelGeom &G,
+                                           const Tab &tab, int nlut, float inv_vmax, float alpha_stop)
+{
+    if (S.k >= S.kend) return true;
+    if (!S.occupied) {
+        // an empty cell: its samples have opacity exactly 0; jump to the
+        // first sample of the next cell
+        const int kn = S.kmin;
+        if (kn >= S.kend) return true;
+        const long long dk = (long long)(kn - S.k);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S.U[a] += dk * V.dU[a];
+        S.k = kn;
+        march_cross(S, V, G, tab);
+        return false;
+    }
+    const int *Mm1 = G.m1;
+    const int ix = int(S.U[0] >> 32), iy = int(S.U[1] >> 32), iz = int(S.U[2] >> 32);
+    const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]);
+    const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
+    const float fx = float(uint32_t(S.U[0])) * 2.3283064365386963e-10f;
+    const float fy = float(uint32_t(S.U[1])) * 2.3283064365386963e-10f;
+    const float fz = float(uint32_t(S.U[2])) * 2.3283064365386963e-10f;
+    if (iz != S.zc) {
+        // the slice pair changes only when the sample's lower corner leaves its slice
+        S.zc = iz;
+        S.za = tab.slice_at(min(max(iz, 0), Mm1[2]));
+        S.zb = tab.slice_at(min(max(iz + 1, 0), Mm1[2]));
+    }
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if constexpr (Tab::kGather) {
+        const bool dx = x1 != x0, dy = y1i != y0i;
+        gather_quad<T>(tab.tex, S.za, x0, y0i, dx, dy, v000, v100, v010, v110);
+        gather_quad<T>(tab.tex, S.zb, x0, y0i, dx, dy, v001, v101, v011, v111);
+    } else {
+        const uint32_t pitch = G.pitch;
+        const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
+        v000 = texel(atlas, S.za + ya + x0);
+        v100 = texel(atlas, S.za + ya + x1);
+        v010 = texel(atlas, S.za + yb + x0);
+        v110 = texel(atlas, S.za + yb + x1);
+        v001 = texel(atlas, S.zb + ya + x0);
+        v101 = texel(atlas, S.zb + ya + x1);
+        v011 = texel(atlas, S.zb + yb + x0);
+        v111 = texel(atlas, S.zb + yb + x1);
+    }
+    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
+    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    const float x = lut_coord(fmaf(fz, c1 - c0, c0), inv_vmax, float(nlut - 1));
+    const int j = min(int(x), nlut - 2);
+    const float fl = x - float(j);
+    const float4 e0 = tab.lut_at(j), e1 = tab.lut_at(j + 1);
+    const float ca = fmaf(fl, e1.w - e0.w, e0.w);
+    const float w = (1.0f - S.A) * ca;
+    S.C0 = fmaf(w, fmaf(fl, e1.x - e0.x, e0.x), S.C0);
+    S.C1 = fmaf(w, fmaf(fl, e1.y - e0.y, e0.y), S.C1);
+    S.C2 = fmaf(w, fmaf(fl, e1.z - e0.z, e0.z), S.C2);
+    S.A += w;
+    ++S.k;
+    if (kCount) ++S.nev;
+    if (S.A >= alpha_stop) return true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) S.U[a] += V.dU[a];
+    if (S.k == S.kmin) march_cross(S, V, G, tab);
+    return S.k >= S.kend;
+}
+
+// Samples a finished ray took: all n unless it stopped early (the samples
+// after its last marked cell are empty and count as taken).
+__device__ __forceinline__ int march_taken(const RayMarch &S, float alpha_stop)
+{
+    return S.A < alpha_stop ? S.n : S.k;
+}
+
 // March the ray of pixel (px, py) of view V through a level; returns the
 // premultiplied (C, A), adds the number of samples taken to `taken` and the
 // number of them evaluated (not skipped as empty) to `evaluated` (kCount;
@@ -227,178 +473,22 @@ __device__ __forceinline__ float4 march_ray(const ViewParams &V, const T *atlas,
                                             int py, uint32_t &taken, uint32_t &evaluated,
                                             DepthRange range = DepthRange{false, 0u, 0u})
 {
-    // ---- FP32 ray set-up, one rounding per operation, fixed order
-    const float sx = __fsub_rn(__fdiv_rn(__fadd_rn(float(px), 0.5f), float(V.W)), 0.5f);
-    const float sy = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn(float(py), 0.5f), float(V.H)));
-    const float sxL = __fmul_rn(sx, V.L), syL = __fmul_rn(sy, V.L);
-    float o[3], d[3];
-    float tmin = -INFINITY, tmax = INFINITY;
-    bool miss = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float t1 = __fadd_rn(V.c[a], __fmul_rn(sxL, V.r[a]));
-        const float t2 = __fadd_rn(t1, __fmul_rn(syL, V.u[a]));
-        o[a] = __fadd_rn(t2, __fmul_rn(V.L, V.b[a]));
-        d[a] = -V.b[a];
-        if (d[a] != 0.0f) {
-            const float inv = V.inv_d[a];  // = __frcp_rn(d[a]), rounded once on the host
-            const float s0 = __fmul_rn(__fsub_rn(0.0f, o[a]), inv);
-            const float s1 = __fmul_rn(__fsub_rn(V.N[a], o[a]), inv);
-            tmin = fmaxf(tmin, fminf(s0, s1));
-            tmax = fminf(tmax, fmaxf(s0, s1));
-        } else if (!(o[a] >= 0.0f && o[a] <= V.N[a])) {
-            miss = true;
-        }
+    const RaySpan R = ray_span(V, px, py);
+    if (R.n <= 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    int k0, kend;
+    if (!ray_range(V, R, range, k0, kend)) {
+        taken += uint32_t(R.n);
+        return make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    int64_t n = 0;
-    if (!miss && tmax > tmin) n = int64_t(floorf(__fdiv_rn(__fsub_rn(tmax, tmin), V.delta)));
-    if (n <= 0) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const int nn = int(n);
-
-    // ---- samples [k0, kend) can reach a marked cell; the others have
-    // opacity exactly 0.  Sample k sits at depth tmin + (k + 1/2) Delta - L,
-    // so k = (depth + L - tmin) / Delta - 1/2; two samples of margin cover
-    // the rounding of this estimate (the raster already adds a voxel).
-    int k0 = 0, kend = nn;
-    if (range.on) {
-        if (range.lo > range.hi) {
-            taken += uint32_t(nn);
-            return make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const float inv_d = 1.0f / V.delta;
-        const float klo = (__uint_as_float(range.lo) - tmin) * inv_d - 2.5f;
-        const float khi = (__uint_as_float(range.hi) - tmin) * inv_d + 2.5f;
-        k0 = int(fminf(fmaxf(klo, 0.0f), float(nn)));
-        kend = int(fminf(fmaxf(khi, 0.0f), float(nn - 1))) + 1;
+    long long U[3];
+    ray_coords(V, R, k0, U);
+    RayMarch S;
+    march_begin(S, V, G, use_skip && V.skip_ok, tab, U, k0, kend, R.n);
+    while (!march_step<T, kCount>(S, V, atlas, G, tab, nlut, inv_vmax, alpha_stop)) {
     }
-
-    // ---- fixed-point level coordinates of sample 0; the step is per view
-    long long U0[3];
-    const long long *dU = V.dU;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) U0[a] = start_coord(o[a], d[a], tmin, 0.5f * V.delta, V.sc_hi[a], V.sc_lo[a]);
-    const int *Mm1 = G.m1;
-    // ---- exact integer DDA over the 8^3 cells of each sample's lower corner:
-    // nxt[a] is the first sample index whose corner is in the next cell along
-    // axis a; with m = |dU| (< 2^32), D = 8 voxels, D = q m + r, the crossing
-    // after one at c (slack e = c m - distance, 0 <= e < m) is at
-    // c + q + (r > e), slack e + (r > e ? m : 0) - r.  Indices past the ray's
-    // end stand for "no further crossing".
-    const bool skip = use_skip && V.skip_ok;
-    constexpr int kInf = 0x7fffffff;
-    int cc[3], nxt[3];
-    uint32_t ee[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        cc[a] = min(max(int((U0[a] + (long long)k0 * dU[a]) >> 32), 0), Mm1[a]) >> 3;  // cell of sample k0
-        nxt[a] = kInf;
-        ee[a] = 0;
-        const int last = Mm1[a] >> 3;
-        if (skip && dU[a] != 0 && (dU[a] > 0 ? cc[a] < last : cc[a] > 0)) {
-            const long long m = dU[a] > 0 ? dU[a] : -dU[a];
-            const long long num = dU[a] > 0 ? ((long long)(8 * cc[a] + 8) << 32) - U0[a]
-                                            : U0[a] - ((long long)(8 * cc[a]) << 32) + 1;
-            // c = ceil(num / m): float estimate, then exact correction
-            const float est = float(num) * V.inv_m[a];
-            if (est < float(n) + 2.0f) {
-                long long c = (long long)est;
-                while (c * m < num) ++c;
-                while (c > 0 && (c - 1) * m >= num) --c;
-                nxt[a] = int(c);
-                ee[a] = uint32_t(c * m - num);
-            }
-        }
-    }
-    auto cross = [&](int a) {
-        const bool fwd = dU[a] > 0;
-        cc[a] += fwd ? 1 : -1;
-        if (fwd ? cc[a] >= (Mm1[a] >> 3) : cc[a] <= 0) {
-            nxt[a] = kInf;  // the last cell this way: clamping keeps the corner in it
-            return;
-        }
-        const uint32_t m = uint32_t(fwd ? dU[a] : -dU[a]);
-        const bool up = V.rr[a] > ee[a];
-        nxt[a] = int(min(uint32_t(nxt[a]) + V.qq[a] + (up ? 1u : 0u), uint32_t(kInf)));
-        ee[a] += (up ? m : 0u) - V.rr[a];
-    };
-    auto marked = [&]() -> bool {
-        const uint32_t word = tab.occ_at((cc[2] * G.gy + cc[1]) * G.wpr + (cc[0] >> 5));
-        return (word >> (cc[0] & 31)) & 1u;
-    };
-    const uint32_t pitch = G.pitch;
-    const float nl1 = float(nlut - 1);
-    const int jmax = nlut - 2;
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-    int k = k0, nev = 0;
-    bool occupied = skip ? marked() : true;  // the current cell's bit, refreshed at every crossing
-    while (k < kend) {
-        if (!occupied) {
-            // an empty cell: its samples have opacity exactly 0; jump to the
-            // first sample of the next cell
-            const int kn = min(min(nxt[0], nxt[1]), nxt[2]);
-            if (kn >= kend) break;
-            k = kn;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (nxt[a] == kn) cross(a);
-            occupied = marked();
-            continue;
-        }
-        long long U[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) U[a] = U0[a] + (long long)k * dU[a];
-        const int ix = int(U[0] >> 32), iy = int(U[1] >> 32), iz = int(U[2] >> 32);
-        const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]), z0i = min(max(iz, 0), Mm1[2]);
-        const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
-        const int z1i = min(max(iz + 1, 0), Mm1[2]);
-        const float fx = float(uint32_t(U[0])) * 2.3283064365386963e-10f;
-        const float fy = float(uint32_t(U[1])) * 2.3283064365386963e-10f;
-        const float fz = float(uint32_t(U[2])) * 2.3283064365386963e-10f;
-        const uint32_t za = tab.slice_at(z0i), zb = tab.slice_at(z1i);
-        float v000, v100, v010, v110, v001, v101, v011, v111;
-        if constexpr (Tab::kGather) {
-            const bool dx = x1 != x0, dy = y1i != y0i;
-            gather_quad<T>(tab.tex, za, x0, y0i, dx, dy, v000, v100, v010, v110);
-            gather_quad<T>(tab.tex, zb, x0, y0i, dx, dy, v001, v101, v011, v111);
-        } else {
-            const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
-            v000 = texel(atlas, za + ya + x0);
-            v100 = texel(atlas, za + ya + x1);
-            v010 = texel(atlas, za + yb + x0);
-            v110 = texel(atlas, za + yb + x1);
-            v001 = texel(atlas, zb + ya + x0);
-            v101 = texel(atlas, zb + ya + x1);
-            v011 = texel(atlas, zb + yb + x0);
-            v111 = texel(atlas, zb + yb + x1);
-        }
-        const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
-        const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
-        const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-        const float x = lut_coord(fmaf(fz, c1 - c0, c0), inv_vmax, nl1);
-        const int j = min(int(x), jmax);
-        const float fl = x - float(j);
-        const float4 e0 = tab.lut_at(j), e1 = tab.lut_at(j + 1);
-        const float ca = fmaf(fl, e1.w - e0.w, e0.w);
-        const float w = (1.0f - A) * ca;
-        C0 = fmaf(w, fmaf(fl, e1.x - e0.x, e0.x), C0);
-        C1 = fmaf(w, fmaf(fl, e1.y - e0.y, e0.y), C1);
-        C2 = fmaf(w, fmaf(fl, e1.z - e0.z, e0.z), C2);
-        A += w;
-        ++k;
-        if (kCount) ++nev;
-        if (A >= alpha_stop) break;
-        if (skip) {
-            bool moved = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (nxt[a] == k) { cross(a); moved = true; }
-            if (moved) occupied = marked();
-        }
-    }
-    if (A < alpha_stop) k = nn;  // not stopped early: every sample was taken (the rest are empty)
-    taken += uint32_t(k);
-    if (kCount) evaluated += uint32_t(nev);
-    return make_float4(C0, C1, C2, A);
+    taken += uint32_t(march_taken(S, alpha_stop));
+    if (kCount) evaluated += uint32_t(S.nev);
+    return make_float4(S.C0, S.C1, S.C2, S.A);
 }
 
 // A per-thread 32-bit count that reached 2^31 goes to the 64-bit total (rare).
