@@ -2,13 +2,15 @@
 // ITS, Alg. 2, partition, Sec. III-A; the top-slice histogram of the
 // histogram filter, Sec. III-D).
 //
-// One HBM pass over the slab.  Each block keeps `copies` private u32
-// sub-histograms in shared memory (warp w uses copy w % copies, so warps
-// rarely collide on a counter), reads the slab as 16-byte vectors with four
-// loads in flight per thread, and adds its counters to the u64 global
-// histogram once at the end.  With at most 256 bins the block instead keeps
-// one counter per (bin, lane), which no two lanes of a warp share.  Elements before the first 16-byte boundary and
-// after the last full vector are counted with scalar loads.
+// One HBM pass over the slab, read as 16-byte vectors with several loads in
+// flight per thread (elements before the first 16-byte boundary and after the
+// last full vector with scalar loads); each block counts into shared memory
+// and adds its counts to the u64 global histogram once at the end.  Shared
+// atomics of a warp that hit one bank in different words wait on one another,
+// so counters are laid out per lane: with at most 256 bins every (bin, lane)
+// has its own counter, in the lane's bank; with more bins that holds for a
+// window of 1024 bins where most values fall, and the rest share one counter
+// per bin.
 #include <algorithm>
 
 #include "mctp_internal.cuh"
@@ -18,83 +20,6 @@ namespace {
 
 constexpr int kHistThreads = 512;
 constexpr int kHistUnroll = 4;
-
-template <typename T, bool kCheckOverflow>
-__device__ __forceinline__ void count_value(uint32_t v, uint32_t *sh, int shift, uint32_t limit,
-                                            uint32_t &ovf)
-{
-    if (kCheckOverflow && v >= limit) {
-        ++ovf;
-        return;
-    }
-    atomicAdd(&sh[v >> shift], 1u);
-}
-
-template <typename T, bool kCheckOverflow>
-__device__ __forceinline__ void count_vector(const uint4 &q, uint32_t *sh, int shift, uint32_t limit,
-                                             uint32_t &ovf)
-{
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (sizeof(T) == 1) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                count_value<T, kCheckOverflow>((w[k] >> (8 * b)) & 0xffu, sh, shift, limit, ovf);
-        } else {
-            count_value<T, kCheckOverflow>(w[k] & 0xffffu, sh, shift, limit, ovf);
-            count_value<T, kCheckOverflow>(w[k] >> 16, sh, shift, limit, ovf);
-        }
-    }
-}
-
-template <typename T, bool kCheckOverflow>
-__global__ void __launch_bounds__(kHistThreads)
-    hist_kernel(const T *__restrict__ base, int64_t n, int64_t head, int64_t nvec, int shift,
-                uint32_t limit, int nbins, int copies, unsigned long long *__restrict__ hist,
-                unsigned long long *__restrict__ overflow)
-{
-    extern __shared__ uint32_t sh_hist[];
-    for (int i = threadIdx.x; i < nbins * copies; i += blockDim.x) sh_hist[i] = 0u;
-    __syncthreads();
-
-    uint32_t *mine = sh_hist + ((threadIdx.x >> 5) % copies) * nbins;
-    uint32_t ovf = 0;
-    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
-    constexpr int E = 16 / sizeof(T);
-
-    // scalar head (before the first 16-byte boundary) and tail
-    const int64_t tail0 = head + nvec * E;
-    for (int64_t i = tid; i < head; i += nthreads)
-        count_value<T, kCheckOverflow>(base[i], mine, shift, limit, ovf);
-    for (int64_t i = tail0 + tid; i < n; i += nthreads)
-        count_value<T, kCheckOverflow>(base[i], mine, shift, limit, ovf);
-
-    // vector body
-    const uint4 *body = reinterpret_cast<const uint4 *>(base + head);
-    int64_t i = tid;
-    for (; i + (kHistUnroll - 1) * nthreads < nvec; i += kHistUnroll * nthreads) {
-        uint4 q[kHistUnroll];
-#pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u) q[u] = ld_stream_v4(body + i + u * nthreads);
-#pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u) count_vector<T, kCheckOverflow>(q[u], mine, shift, limit, ovf);
-    }
-    for (; i < nvec; i += nthreads) count_vector<T, kCheckOverflow>(ld_stream_v4(body + i), mine, shift, limit, ovf);
-
-    __syncthreads();
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-        uint32_t s = 0;
-        for (int c = 0; c < copies; ++c) s += sh_hist[c * nbins + b];
-        if (s) atomicAdd(&hist[b], (unsigned long long)s);
-    }
-    if (kCheckOverflow) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
-        if ((threadIdx.x & 31) == 0 && ovf) atomicAdd(overflow, (unsigned long long)ovf);
-    }
-}
 
 // At most 256 bins: one counter per (bin, lane) in shared memory, bin-major
 // with the lane fastest, so the 32 atomics of a warp instruction always fall
@@ -172,6 +97,147 @@ __global__ void __launch_bounds__(kHistThreads)
     }
 }
 
+// More than 256 bins: one counter per (bin, lane) does not fit in shared
+// memory for all bins, so the block keeps it for a window of 1024 bins, where
+// most values fall (the grey values of a scan cluster in a narrow range), and
+// one counter per bin for the rest.  In the window a lane always adds to a
+// word of its own bank, so a warp's atomics never wait on one another; values
+// outside it share the plain table.  Every block picks the same window: the
+// 1024 bins holding the most of 8192 values sampled evenly over the slab.
+// Any window gives the same counts; it only changes how fast they are made.
+constexpr int kWinBins = 1024;
+constexpr int kWinThreads = 1024;
+constexpr int kWinUnroll = 8;
+constexpr int kCoarse = 64;
+
+template <typename T, bool kCheckOverflow>
+__global__ void __launch_bounds__(kWinThreads, 1)
+    hist_window_kernel(const T *__restrict__ base, int64_t n, int64_t head, int64_t nvec, int shift, uint32_t limit,
+                       int nbins, unsigned long long *__restrict__ hist, unsigned long long *__restrict__ overflow)
+{
+    extern __shared__ uint32_t sh_win[];  // kWinBins * 32 lane columns, then nbins + 1 plain counters
+    __shared__ uint32_t coarse[kCoarse];
+    __shared__ int sh_lo;
+    uint32_t *plain = sh_win + kWinBins * 32;
+    for (int i = threadIdx.x; i < kWinBins * 32 + nbins + 1; i += blockDim.x) sh_win[i] = 0u;
+    if (threadIdx.x < kCoarse) coarse[threadIdx.x] = 0u;
+    __syncthreads();
+    constexpr int E = 16 / sizeof(T);
+    const int lane = threadIdx.x & 31;
+    const int cshift = __ffs(nbins) - 1 - 6;  // coarse bin = bin >> cshift (nbins = 64 << cshift)
+
+    // ---- the window: densest run of coarse bins in an even sample
+    if (nvec > 0) {
+        const int64_t at = (int64_t(threadIdx.x) * nvec) / kWinThreads;
+        const uint4 q = ld_stream_v4(reinterpret_cast<const uint4 *>(base + head) + at);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int b = 0; b < 4 / int(sizeof(T)); ++b) {
+                const uint32_t v = sizeof(T) == 1 ? (w[k] >> (8 * b)) & 0xffu : (w[k] >> (16 * b)) & 0xffffu;
+                if (!kCheckOverflow || v < limit) atomicAdd(&coarse[(v >> shift) >> cshift], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // prefix sums over the 64 coarse bins, then the best run of `wc` of them
+        const int wc = min(kCoarse, (kWinBins << 6) / nbins);
+        uint32_t a = coarse[2 * lane], b = coarse[2 * lane + 1];
+        uint32_t s = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        // inclusive prefix P[i] = coarse[0] + ... + coarse[i]
+        const uint32_t p1 = s, p0 = s - b;
+        __shared__ uint32_t P[kCoarse];
+        P[2 * lane] = p0;
+        P[2 * lane + 1] = p1;
+        __syncwarp();
+        uint32_t best = 0;
+        int best_c = kCoarse;  // none yet
+        for (int c = lane; c + wc <= kCoarse; c += 32) {
+            const uint32_t m = P[c + wc - 1] - (c > 0 ? P[c - 1] : 0u);
+            if (best_c == kCoarse || m > best) {
+                best = m;
+                best_c = c;
+            }
+        }
+        // the lowest start among the largest sums
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, best_c, o);
+            if (ob > best || (ob == best && oc < best_c)) {
+                best = ob;
+                best_c = oc;
+            }
+        }
+        if (best_c == kCoarse) best_c = 0;
+        if (lane == 0) sh_lo = best_c << cshift;
+    }
+    __syncthreads();
+    const uint32_t lo = uint32_t(sh_lo);
+    // branch-free count: values >= 2^bits go to slot nbins (the overflow), a
+    // value in the window to its lane's word of the window, the rest to the
+    // plain table; byte offsets into shared memory
+    const uint32_t nb = uint32_t(nbins);
+    uint32_t *const hot_lane = sh_win + lane;
+    auto count = [&](uint32_t v) {
+        uint32_t bin = v >> shift;
+        if (kCheckOverflow) bin = min(bin, nb);
+        const uint32_t d = bin - lo;  // wraps for bins below the window
+        uint32_t *const at = d < uint32_t(kWinBins) ? hot_lane + (d << 5) : plain + bin;
+        atomicAdd(at, 1u);
+    };
+    auto count_vec = [&](const uint4 &q) {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sizeof(T) == 1) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) count((w[k] >> (8 * b)) & 0xffu);
+            } else {
+                count(w[k] & 0xffffu);
+                count(w[k] >> 16);
+            }
+        }
+    };
+
+    // ---- one pass over the slab
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
+    const int64_t tail0 = head + nvec * E;
+    for (int64_t i = tid; i < head; i += nthreads) count(base[i]);
+    for (int64_t i = tail0 + tid; i < n; i += nthreads) count(base[i]);
+    const uint4 *body = reinterpret_cast<const uint4 *>(base + head);
+    int64_t i = tid;
+    for (; i + (kWinUnroll - 1) * nthreads < nvec; i += kWinUnroll * nthreads) {
+        uint4 q[kWinUnroll];
+#pragma unroll
+        for (int u = 0; u < kWinUnroll; ++u) q[u] = ld_stream_v4(body + i + u * nthreads);
+#pragma unroll
+        for (int u = 0; u < kWinUnroll; ++u) count_vec(q[u]);
+    }
+    for (; i < nvec; i += nthreads) count_vec(ld_stream_v4(body + i));
+    __syncthreads();
+
+    // ---- the block's counts into the global histogram; slot nbins is the overflow
+    for (int b = threadIdx.x; b <= nbins; b += blockDim.x) {
+        const uint32_t d = uint32_t(b) - lo;
+        unsigned long long sum = 0;
+        if (d < uint32_t(kWinBins)) {
+            for (int l = 0; l < 32; ++l) sum += sh_win[(d << 5) + ((l + d) & 31)];  // rotated: no bank conflicts
+        } else {
+            sum = plain[b];
+        }
+        if (sum) atomicAdd(b < nbins ? &hist[b] : overflow, sum);
+    }
+}
+
 // Bins too many for shared memory (nbins > 16384): count straight into the
 // global u64 histogram.
 template <typename T>
@@ -219,29 +285,27 @@ int launch_hist(const T *base, int64_t n, int bits, int nbins, uint64_t *hist, u
         kern<<<unsigned(grid), kHistThreads, smem, s>>>(base, n, head, nvec, shift, limit, nbins, h, ov);
         return launch_status();
     }
-    // copies: as many private sub-histograms as fit in 32 KB, up to one per warp (more copies
-    // and fewer CTAs per SM measured slower: 4096 bins, 4 copies 2.955 ms, 2 copies 2.879 ms)
-    int copies = 1;
-    while (copies < kHistThreads / 32 && size_t(copies * 2) * nbins * 4 <= 32768) copies *= 2;
-    const size_t smem = size_t(copies) * nbins * 4;
-    const uintptr_t addr = reinterpret_cast<uintptr_t>(base);
-    int64_t head = int64_t(((16 - (addr & 15)) & 15) / sizeof(T));
-    if (head > n) head = n;
-    const int64_t nvec = (n - head) / (16 / int64_t(sizeof(T)));
-
-    auto kern = check ? hist_kernel<T, true> : hist_kernel<T, false>;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHistThreads, smem);
-    per_sm = std::max(per_sm, 1);
-    int64_t want = (nvec + int64_t(kHistThreads) * kHistUnroll - 1) / (int64_t(kHistThreads) * kHistUnroll);
-    int64_t grid = std::min<int64_t>(int64_t(per_sm) * num_sms(), std::max<int64_t>(want, 1));
-    // keep every per-block u32 counter below 2^31
-    grid = std::max<int64_t>(grid, (n >> 30) + 1);
-    grid = std::min<int64_t>(grid, 0x7fffffff);
-    kern<<<unsigned(grid), kHistThreads, smem, s>>>(base, n, head, nvec, shift, limit, nbins, copies, h, ov);
-    return launch_status();
+    if (nbins <= 16384) {
+        const size_t smem = (size_t(kWinBins) * 32 + size_t(nbins) + 1) * 4;
+        int64_t head = int64_t(((16 - (addr0 & 15)) & 15) / sizeof(T));
+        if (head > n) head = n;
+        const int64_t nvec = (n - head) / (16 / int64_t(sizeof(T)));
+        auto kern = check ? hist_window_kernel<T, true> : hist_window_kernel<T, false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+            return MCTP_ECUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWinThreads, smem) != cudaSuccess)
+            return MCTP_ECUDA;
+        per_sm = std::max(per_sm, 1);
+        const int64_t want = (nvec + int64_t(kWinThreads) * kWinUnroll - 1) / (int64_t(kWinThreads) * kWinUnroll);
+        int64_t grid = std::min<int64_t>(int64_t(per_sm) * num_sms(), std::max<int64_t>(want, 1));
+        // every block counts fewer than 2^31 values, so no shared counter wraps
+        grid = std::max<int64_t>(grid, (n >> 31) + 1);
+        grid = std::min<int64_t>(grid, 0x7fffffff);
+        kern<<<unsigned(grid), kWinThreads, smem, s>>>(base, n, head, nvec, shift, limit, nbins, h, ov);
+        return launch_status();
+    }
+    return MCTP_EINVAL;  // not reached: nbins > 16384 takes the global kernel above
 }
 
 }  // namespace
