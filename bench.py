@@ -157,6 +157,46 @@ def peaks():
     return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
+def sm_count(device=None) -> int:
+    """SMs of the GPU, queried from the device."""
+    import torch
+    return int(torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count)
+
+
+def fp32_peak(pk, device=None):
+    """Nominal FP32 rate (TFLOP/s): SMs (queried) x 128 FP32 lanes x 2 flop (FMA) x the maximum SM clock
+    (from MEASURED_PEAKS.json when present); a figure from unit counts, not a measurement."""
+    return sm_count(device) * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+
+
+FP32_PEAK_SOURCE = "nominal: SMs (queried) x 128 FP32 lanes x 2 flop x maximum SM clock"
+FLOPS_SOURCE = ("hand count of the FP32 operations of one evaluated sample: trilinear 21, normalisation 2, "
+                "LUT coordinate 3, LUT lerps 12, compositing 9, position step 1")
+
+
+def render_issue_roofline(evaluated, render_s, pk, device=None):
+    """Issue-rate view of the renderer, which is bound by instruction issue, not by its FP32 work: warp
+    instructions per evaluated sample from an ncu count (profiles/render_counters.json, kept only while
+    the kernel's sources are unchanged) x evaluated samples / render time, against SMs x 4 schedulers x
+    one warp instruction per clock."""
+    path = os.path.join(ROOT, "profiles", "render_counters.json")
+    peak = sm_count(device) * 4 * pk["sm_max_mhz"] * 1e6
+    out = dict(unit="warp instructions/s", peak=peak, peak_source="nominal: SMs x 4 schedulers x max SM clock",
+               warp_inst_per_evaluated_sample=None, thread_inst_per_evaluated_sample=None, achieved=None, frac=None)
+    if not os.path.exists(path):
+        return out
+    rec = json.load(open(path))
+    if source_sha256(KERNEL_SOURCES["render"]) != rec.get("source_sha256"):
+        return out
+    wpe = rec["warp_inst_executed"] / rec["evaluated_samples"]
+    out.update(warp_inst_per_evaluated_sample=wpe,
+               thread_inst_per_evaluated_sample=rec["thread_inst_executed"] / rec["evaluated_samples"],
+               lanes_per_warp_inst=rec["thread_inst_executed"] / rec["warp_inst_executed"],
+               achieved=wpe * evaluated / render_s, frac=wpe * evaluated / render_s / peak,
+               counters_from=rec.get("workload"))
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -237,6 +277,89 @@ def job_rate(units_per_rank_step: float, steps: int, ws: int, seconds: float) ->
 
 # --------------------------------------------------------------- CPU oracle
 
+def host_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _pool_map(fn, items, threads):
+    """fn over items on `threads` host threads (the oracle's C calls release the GIL)."""
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(fn, items))
+
+
+def oracle_level0_threaded(vol_np, bits, M, keep, threads):
+    """The oracle's level 0 of vol_np computed in z-slabs on host threads.
+    Output slice z covers source slices [floor(z N / M), floor((z + 1) N / M));
+    where z N / M is an integer a slab of g = M / gcd(N, M) output slices has
+    exactly the footprints of the whole volume, so the slabs' levels stack to
+    the whole level.  Returns (level, slabs)."""
+    import math
+    import oracle
+    nz = vol_np.shape[0]
+    g = M[2] // math.gcd(nz, M[2])
+    nslab = M[2] // g
+    src_per = nz // nslab
+    slabs = _pool_map(lambda i: oracle.downsample(vol_np[i * src_per:(i + 1) * src_per], bits, (M[0], M[1], g), keep),
+                      range(nslab), threads)
+    return np.concatenate(slabs, axis=0), nslab
+
+
+def oracle_full_step(wl, vol_np, threads=None):
+    """The oracle on the full step's own data, on the host's cores: the
+    histogram of the whole volume (threads over z-slabs; the slab counts add
+    up exactly), Otsu, the level-0 slicemap of the whole volume (threads over
+    source slabs whose footprints fill whole output slices, so each slab's
+    level equals its part of the full level), the coarser levels, and one
+    full view of the turntable (threads over rays).  The step's other views
+    are extrapolated from that one.  Returns a cpu_baseline record."""
+    import oracle
+    import phantom
+    threads = threads or host_threads()
+    spec, bits, nbins = wl["spec"], wl["bits"], wl["nbins"]
+    nz, ny, nx = vol_np.shape
+    M = wl["level0"]
+    t = {}
+    t0 = time.perf_counter()
+    zs = np.linspace(0, nz, min(threads, nz) + 1).astype(int)
+    parts = _pool_map(lambda i: oracle.histogram(vol_np, bits, nbins, int(zs[i]), int(zs[i + 1])),
+                      range(len(zs) - 1), threads)
+    hist = sum(p[0] for p in parts)
+    t["histogram"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T, _ = oracle.otsu(hist)
+    keep = oracle.keep_threshold(nbins, T)
+    t["threshold"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    level0, nslab = oracle_level0_threaded(vol_np, bits, M, keep, threads)
+    dims = [M]
+    for _ in range(1, wl["nlevels"]):
+        dims.append(tuple(d // 2 for d in dims[-1]))
+    lv = level0
+    for d in dims[1:]:
+        lv = oracle.downsample(lv, bits, d)
+    t["slicemap"] = time.perf_counter() - t0
+    size = wl["size"]
+    lut = phantom.ramp_lut(256)
+    pix = np.arange(size * size, dtype=np.int64)
+    chunks = np.array_split(pix, threads * 8)
+    t0 = time.perf_counter()
+    outs = _pool_map(lambda c: oracle.render(level0, bits, (spec.nx, spec.ny, spec.nz), lut, 0.0, 0.0, size, size,
+                                             0.5, 0.99, 0.0, pixels=c), chunks, threads)
+    t["render_one_view"] = time.perf_counter() - t0
+    view_samples = float(sum(o["nsamp"][:, 1].sum() for o in outs))
+    nviews = wl["nviews"]
+    step_s = t["histogram"] + t["threshold"] + t["slicemap"] + nviews * t["render_one_view"]
+    samples = view_samples * nviews
+    return dict(value=samples / step_s, unit=UNIT, cores=threads, host_cpus=os.cpu_count(), kind="oracle",
+                extrapolated=f"render: 1 of {nviews} views measured, the step's time counts it {nviews} times",
+                seconds=dict(t, step=step_s), samples_one_view=int(view_samples),
+                sample=f"oracle (C, {threads} threads): {nbins}-bin histogram of the whole {vol_np.nbytes / 1e9:.1f} GB "
+                       f"volume, Otsu (T={T}), level 0 ({M[0]}x{M[1]}x{M[2]}) of the whole volume in {nslab} "
+                       f"slabs and the coarser levels, one full {size}x{size} view (az 0) of level 0; "
+                       f"{sum(t.values()):.1f} s measured")
+
+
 def oracle_sample(wl, slab=None, npix=8192):
     """Time the oracle on a bounded sample of the workload and extrapolate its
     step time.  Sample: the histogram and slicemap of a 96-slice slab around
@@ -287,7 +410,25 @@ def oracle_sample(wl, slab=None, npix=8192):
     return step_s, samples_step, text
 
 
+def generate_host(spec, threads=None):
+    """The seeded phantom written on the host's cores, slab by slab."""
+    import phantom
+    threads = threads or host_threads()
+    vol = np.empty(spec.shape, dtype=np.uint8 if spec.esize == 1 else np.uint16)
+    zs = np.linspace(0, spec.nz, min(spec.nz, 4 * threads) + 1).astype(int)
+
+    def one(i):
+        z0, z1 = int(zs[i]), int(zs[i + 1])
+        if z1 > z0:
+            vol[z0:z1] = phantom.generate_cpu(spec, ((0, spec.nx), (0, spec.ny), (z0, z1)))
+    _pool_map(one, range(len(zs) - 1), threads)
+    return vol
+
+
 def run_reference(args, wl):
+    """The reference arm: this build's CPU oracle (the paper has no code) on
+    the same workload, every step the full step of oracle_full_step on the
+    host's cores; the warm-up steps are one slab's histogram each."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return 0
@@ -295,24 +436,18 @@ def run_reference(args, wl):
     oracle.build()
     import phantom
     phantom.build(gpu=False)
-    spec = wl["spec"]
-    nz_s = min(spec.nz, 96)
-    zs = spec.nz // 2 - nz_s // 2
-    slab = phantom.generate_cpu(spec, ((0, spec.nx), (0, spec.ny), (zs, zs + nz_s)))
-    vals = []
-    text = ""
-    for i in range(args.warmup + args.steps):
-        step_s, samples_step, text = oracle_sample(wl, slab)
-        if i >= args.warmup:
-            vals.append((step_s, samples_step))
-    step_s = statistics.median(v[0] for v in vals)
-    samples = statistics.median(v[1] for v in vals)
-    value = samples / step_s
+    vol = generate_host(wl["spec"])
+    for _ in range(args.warmup):
+        oracle.histogram(vol[: max(1, vol.shape[0] // 64)], wl["bits"], wl["nbins"])
+    recs = [oracle_full_step(wl, vol) for _ in range(args.steps)]
+    rec = sorted(recs, key=lambda r: r["value"])[len(recs) // 2]
+    value = rec["value"]
+    step_s = rec["seconds"]["step"]
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                 warmup=args.warmup, ms_per_step=step_s * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="u16/f64", data="synthetic",
                 config=dict(workload=wl["desc"], l2="n/a (CPU)"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=text),
+                cpu_baseline=rec,
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -447,7 +582,7 @@ def run_gpu(args, wl):
         "threshold": dict(bound="alu", flops=0, unit="TFLOP/s"),
         "entropy": dict(bound="hbm", bytes=image_bytes, unit="GB/s"),
     }
-    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    fp32 = fp32_peak(pk, dev)
     traffic = measured_traffic() if args.workload == "full" else {}
     roof = {}
     for name, k in kernels.items():
@@ -458,9 +593,15 @@ def run_gpu(args, wl):
                               frac=ach / pk["hbm_gbs"], ms=stage_ms[name], traffic=traffic.get(name))
         else:
             ach = k["flops"] / t / 1e12
-            roof[name] = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s",
-                              frac=ach / fp32_peak, ms=stage_ms[name], traffic=traffic.get(name))
+            roof[name] = dict(bound="alu", achieved=ach, peak=fp32, unit="TFLOP/s",
+                              frac=ach / fp32, ms=stage_ms[name], traffic=traffic.get(name),
+                              peak_source=FP32_PEAK_SOURCE)
     roof["render"]["compulsory_hbm_gbs"] = wl["nviews"] * level0_bytes / (stage_ms["render"] / 1e3) / 1e9
+    roof["render"]["flops_per_sample"] = FP32_FLOPS_PER_SAMPLE
+    roof["render"]["flops_source"] = FLOPS_SOURCE
+    roof["render"]["issue"] = render_issue_roofline(evaluated_per_step, stage_ms["render"] / 1e3, pk, dev)
+    for name in ("histogram", "slicemap", "texture", "entropy"):
+        roof[name]["peak_source"] = pk["source"] + " HBM copy bandwidth"
     dominant = max(stage_ms, key=stage_ms.get)
     value = job_rate(samples_per_step, args.steps, ws, elapsed)
     best_view = int(pipe.best.item())
@@ -479,9 +620,11 @@ def run_gpu(args, wl):
         slicemap_gbs=roof["slicemap"]["achieved"], slicemap_frac_of_hbm_peak=roof["slicemap"]["frac"],
         histogram_gbs=roof["histogram"]["achieved"],
         render_samples_per_s=samples_per_step / (stage_ms["render"] / 1e3),
+        render_evaluated_samples_per_s=evaluated_per_step / (stage_ms["render"] / 1e3),
+        evaluated_share=evaluated_per_step / samples_per_step,
         latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
         stage_ms=stage_ms,
-        roofline=dict(roof[dominant], kernel=dominant, peak_source=pk["source"]),
+        roofline=dict(roof[dominant], kernel=dominant),
         roofline_by_kernel=roof,
         gpu_launches=launches_per_step(wl, len(views), sum(t is not None for t in pipe.sm.textures or []))
         * args.steps,
@@ -489,19 +632,109 @@ def run_gpu(args, wl):
         e2e=dict(value=samples_per_step / e2e_s, unit=UNIT, h2d_bytes_per_step=vol_bytes,
                  d2h_bytes_per_step=image_bytes, ms_per_step=e2e_s * 1e3),
     )
+    if not args.no_next_rows and args.workload == "full":
+        line["next_rows"] = next_rows_record(dev)
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        nz_s = min(spec.nz, 96)
-        zs = spec.nz // 2 - nz_s // 2
-        del vol_host
-        step_s, samples_step, text = oracle_sample(wl, vol[zs:zs + nz_s].cpu().numpy(), npix=65536)
-        line["cpu_baseline"] = dict(value=samples_step / step_s, unit=UNIT, cores=1, kind="oracle", sample=text)
+        line["cpu_baseline"] = oracle_full_step(wl, vol_host.numpy())
+    del vol_host
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def next_rows_record(dev, rate: float = 4000.0, requests: int = 400):
+    """Compact measurements of the batched renderer and the server beside the
+    main step: the first 8 volumes of the batched workload (u8, axes
+    ~U{384..1024}, 256^3 levels, 12 views 512^2 each) rendered by one batched
+    launch, by one render_views launch per volume and by one per view (images
+    and sample counts asserted equal); and a Poisson stream of requests
+    (512^2 / 1024^2, random azimuth and elevation, 8 transfer functions) on
+    those 8 slicemaps served by the continuous-batching server and by
+    per-view launches, p50/p99 latency and samples/s."""
+    import torch
+    import phantom
+    import paper_2311_15038_gb300 as mctp
+    from paper_2311_15038_gb300 import batch as bt
+    from paper_2311_15038_gb300 import pipeline as pl
+    from paper_2311_15038_gb300 import serve as sv
+    wl = workload("batch8")
+    stream = torch.cuda.Stream(dev)
+    vols = []
+    for sp in wl["specs"]:
+        v = torch.empty(sp.shape, dtype=torch.uint8, device=dev)
+        phantom.generate_gpu(sp, v)
+        vols.append(v)
+    lut = torch.from_numpy(phantom.ramp_lut(256)).to(dev)
+    views = pl.turntable(wl["nviews"], wl["size"], 0, 0.5, wl["elevation"], wl["az_step"])
+    pipe = bt.BatchPipeline([bt.BatchItem(v, 8, views, 0) for v in vols], wl["level0"], wl["nlevels"], lut,
+                            wl["nbins"], "otsu", 0.99, device=dev, stream=stream)
+    pipe.autotune(reps=1)
+    torch.cuda.synchronize(dev)
+    px = wl["size"] * wl["size"] * 4
+    plain = torch.empty_like(pipe.images)
+    s_vol = [torch.empty(1, dtype=torch.uint64, device=dev) for _ in vols]
+    s_view = [torch.empty(1, dtype=torch.uint64, device=dev) for _ in pipe.views]
+
+    def per_volume():
+        for i, sm in enumerate(pipe.slicemaps):
+            mctp.render_views(sm, views, lut, 0.99, plain[i * len(views) * px:(i + 1) * len(views) * px], s_vol[i],
+                              stream)
+
+    def per_view():
+        for j, v in enumerate(pipe.views):
+            mctp.render_views(pipe.slicemaps[pipe.view_slicemap[j]], [v], lut, 0.99, plain[j * px:(j + 1) * px],
+                              s_view[j], stream)
+
+    def timed(fn, reps=3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            fn()
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+    ms = dict(batched=timed(pipe.render))
+    samples = int(pipe.samples.item())
+    ref = pipe.images.clone()
+    ms["per_volume"] = timed(per_volume)
+    torch.cuda.synchronize(dev)
+    equal = torch.equal(plain, ref) and sum(int(s.item()) for s in s_vol) == samples
+    ms["per_view"] = timed(per_view)
+    torch.cuda.synchronize(dev)
+    equal = equal and torch.equal(plain, ref) and sum(int(s.item()) for s in s_view) == samples
+    assert equal, "batched images differ from the per-volume / per-view launches"
+    batch = dict(workload=wl["desc"], views=len(pipe.views), samples=samples, render_ms=ms,
+                 samples_per_s={k: samples / (t / 1e3) for k, t in ms.items()},
+                 speedup_vs_per_view=ms["per_view"] / ms["batched"], images_equal=True,
+                 tuning=dict(warp_w=pipe.tuning.warp_w, chunk=pipe.tuning.chunk, ctas_per_sm=pipe.tuning.ctas_per_sm))
+    # ---- serving the same slicemaps
+    luts = torch.from_numpy(np.stack(phantom.preset_luts())).to(dev)
+    serving = {}
+    for name, cfg in (("per_view", dict(mode="per_view", max_batch_views=1, max_inflight=1)),
+                      ("batched", dict(mode="batched", max_batch_views=64, max_inflight=2))):
+        srv = sv.Server(pipe.slicemaps, luts, 2 << 30, **cfg)
+        try:
+            sv.run_trace(srv, sv.poisson_trace(2000.0, 100, len(vols), luts.shape[0], seed=98))
+            trace = sv.poisson_trace(rate, requests, len(vols), luts.shape[0], seed=5)
+            s0 = srv.stats()["samples"]
+            done = sv.run_trace(srv, trace)
+            s1 = srv.stats()["samples"]
+        finally:
+            srv.close()
+        lat = np.array([f.t_done - a for a, f, _ in done]) * 1e3
+        span = max(f.t_done for _, f, _ in done) - min(a for a, _, _ in done)
+        serving[name] = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                             requests_per_s=len(done) / span, samples_per_s=(s1 - s0) / span)
+    serving = dict(rate_per_s=rate, requests=requests, slicemaps=len(vols), **serving)
+    del pipe, vols, plain
+    torch.cuda.empty_cache()
+    return dict(batched_render=batch, serving=serving)
 
 
 def run_batch(args, wl):
@@ -666,13 +899,14 @@ def run_batch(args, wl):
         return 0
 
     pk = peaks()
-    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    fp32 = fp32_peak(pk, dev)
     atlas_bytes = sum(sm.nbytes for sm in pipe.slicemaps)
     prep_bytes = 2 * vol_bytes + atlas_bytes   # histogram read + slicemap read + atlas writes
     render_s = stage_ms["render"] / 1e3
     ach = FP32_FLOPS_PER_SAMPLE * evaluated_per_step / render_s / 1e12
-    roof = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak, kernel="render",
-                ms=stage_ms["render"], traffic=None, peak_source="FP32 issue rate at the maximum SM clock")
+    roof = dict(bound="alu", achieved=ach, peak=fp32, unit="TFLOP/s", frac=ach / fp32, kernel="render",
+                ms=stage_ms["render"], traffic=None, peak_source=FP32_PEAK_SOURCE, flops_source=FLOPS_SOURCE,
+                evaluated_samples_per_s=evaluated_per_step / render_s)
     value = job_rate(samples_per_step, args.steps, ws, elapsed)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
@@ -705,7 +939,8 @@ def run_batch(args, wl):
         nz_s = min(sp.nz, 96)
         zs = sp.nz // 2 - nz_s // 2
         step_s, samples_step, text = oracle_sample(wl0, vols[0][zs:zs + nz_s].cpu().numpy(), npix=65536)
-        line["cpu_baseline"] = dict(value=samples_step / step_s, unit=UNIT, cores=1, kind="oracle",
+        line["cpu_baseline"] = dict(value=samples_step / step_s, unit=UNIT, cores=1, host_cpus=os.cpu_count(),
+                                    kind="oracle", extrapolated="from a 96-slice slab and 65536 rays to the step",
                                     sample="volume 0 of the batch: " + text)
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -918,7 +1153,7 @@ def run_fit(args, wl):
         torch.distributed.destroy_process_group()
         return 0
     pk = peaks()
-    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    fp32 = fp32_peak(pk, dev)
     it_s = elapsed / args.steps
     ach = FP32_FLOPS_PER_SAMPLE * samples_fwd / (stage_ms["forward"] / 1e3) / 1e12
     line = dict(
@@ -933,9 +1168,9 @@ def run_fit(args, wl):
         adjoint_samples_per_s=samples_fwd / (stage_ms["adjoint"] / 1e3),
         loss=dict(start=loss0, end=loss1, iterations=args.warmup + args.steps + e2e_steps, psnr_start_db=psnr(loss0),
                   psnr_end_db=psnr(loss1)),
-        roofline=dict(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                      kernel="dense_forward_kernel", traffic=None,
-                      peak_source="FP32 issue rate at the maximum SM clock"),
+        roofline=dict(bound="alu", achieved=ach, peak=fp32, unit="TFLOP/s", frac=ach / fp32,
+                      kernel="dense_forward_kernel", traffic=None, peak_source=FP32_PEAK_SOURCE,
+                      flops_source=FLOPS_SOURCE),
         cpu_baseline=fit_oracle_baseline(fit, fviews[0], (spec.nx, spec.ny, spec.nz)),
         gpu_launches=5 * args.steps,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
@@ -1075,9 +1310,8 @@ def run_serve(args, wl):
         per_view_latency_ms=dict(p50=p["p50_ms"], p99=p["p99_ms"]),
         serving=results,
         roofline=dict(bound="alu", achieved=FP32_FLOPS_PER_SAMPLE * eval_share * b["samples_per_s"] / 1e12,
-                      peak=152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12, unit="TFLOP/s",
-                      frac=FP32_FLOPS_PER_SAMPLE * eval_share * b["samples_per_s"] / 1e12
-                      / (152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12),
+                      peak=fp32_peak(pk, dev), unit="TFLOP/s", peak_source=FP32_PEAK_SOURCE, flops_source=FLOPS_SOURCE,
+                      frac=FP32_FLOPS_PER_SAMPLE * eval_share * b["samples_per_s"] / 1e12 / fp32_peak(pk, dev),
                       kernel="render_batch_kernel", traffic=None, evaluated_share=eval_share,
                       note="evaluated samples/s over the wall time of the top rate, so idle gaps count against it; "
                            "the evaluated share is from one counted batch of 256 requests of that rate"),
@@ -1103,6 +1337,8 @@ def main():
     ap.add_argument("--workload", default="full",
                     choices=["full", "mid", "slab", "small", "batch", "batch8", "serve", "fit", "thresholds"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip the batched-render and serving sub-record of the full workload's line")
     ap.add_argument("--render-tuning", default=None, metavar="WARP_W,CHUNK,CTAS",
                     help="fixed launch shape of the work-queue renderer (default: autotuned after warm-up)")
     args = ap.parse_args()

@@ -8,8 +8,6 @@
 
 namespace mctp {
 
-constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
-
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int log2_exact(int64_t v)
@@ -54,18 +52,18 @@ inline int launch_status()
     return cudaGetLastError() == cudaSuccess ? MCTP_OK : MCTP_ECUDA;
 }
 
+// SMs of the current device, queried once per device (grid sizes are
+// multiples of it); 1 if the query fails, which keeps every launch valid.
 inline int num_sms()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            n = v;
-        else
-            n = kNumSMs;
-    }
-    return n;
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    if (dev < 64) cached[dev] = v;
+    return v;
 }
 
 // Depth bounds of render_batch_impl: off, on (the workspace must hold them),
