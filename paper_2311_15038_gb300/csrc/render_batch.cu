@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_prep_kernel(const __grid_
     const int z1 = min(p.mz, (part + 1) * zper);
     for (int z = part * zper + threadIdx.x; z < z1; z += blockDim.x) {
         const int row = z / p.tiles_x, col = z - row * p.tiles_x;
-        p.slice_off[z] = p.tex ? uint32_t(col * p.mx) | (uint32_t(row * p.my) << 16)
+        // with a texture: the first interior texel of the slice's padded cell
+        p.slice_off[z] = p.tex ? uint32_t(col * (p.mx + 2) + 1) | (uint32_t(row * (p.my + 2) + 1) << 16)
                                : uint32_t(int64_t(row) * p.my * p.pitch + int64_t(col) * p.mx);
     }
     if (use_skip) {

@@ -172,8 +172,9 @@ struct CachedTables {
 };
 
 // Atlas texture of the level (mctp_atlas_texture_*): slice_at(z) is then the
-// texel origin of slice z's tile, x | y << 16, and the four in-slice corners
-// of a sample come from one gather.
+// texel x | y << 16 where slice z's tile starts inside its padded cell (every
+// tile has a one-texel border repeating its edges), and the four in-slice
+// corners of a sample come from one gather.
 template <bool kLutShared>
 struct GatherTables {
     static constexpr bool kGather = true;
@@ -190,22 +191,22 @@ template <typename T> struct Quad;
 template <> struct Quad<uint8_t> { using type = uchar4; };
 template <> struct Quad<uint16_t> { using type = ushort4; };
 
-// Corners (x0, y0), (x1, y0), (x0, y1), (x1, y1) of the slice whose tile
-// starts at texel `origin`; x1 is x0 + 1 or, clamped at the level's edge,
-// x0 (likewise y1).  The gather at texel coordinate (X + 1, Y + 1) returns the
-// 2x2 block whose lower corner is (X, Y), in the order (X, Y+1), (X+1, Y+1),
-// (X+1, Y), (X, Y) (the bilinear footprint order of texture gathers).
+// Corners (ix, iy), (ix + 1, iy), (ix, iy + 1), (ix + 1, iy + 1) of the slice
+// whose tile starts at texel `origin`, for ix in [-1, mx - 1] and iy in
+// [-1, my - 1]: the padded cell's border holds the clamped values.  The
+// gather at texel coordinate (X + 1, Y + 1) returns the 2x2 block whose lower
+// corner is (X, Y), in the order (X, Y+1), (X+1, Y+1), (X+1, Y), (X, Y) (the
+// bilinear footprint order of texture gathers).
 template <typename T>
-__device__ __forceinline__ void gather_quad(cudaTextureObject_t tex, uint32_t origin, int x0, int y0, bool dx,
-                                            bool dy, float &v00, float &v10, float &v01, float &v11)
+__device__ __forceinline__ void gather_quad(cudaTextureObject_t tex, uint32_t origin, int ix, int iy, float &v00,
+                                            float &v10, float &v01, float &v11)
 {
-    const float gx = float(int(origin & 0xffffu) + x0 + 1), gy = float(int(origin >> 16) + y0 + 1);
+    const float gx = float(int(origin & 0xffffu) + ix + 1), gy = float(int(origin >> 16) + iy + 1);
     const typename Quad<T>::type g = tex2Dgather<typename Quad<T>::type>(tex, gx, gy, 0);
-    const float a = float(g.w), b = float(g.z), c = float(g.x), d = float(g.y);
-    v00 = a;
-    v10 = dx ? b : a;
-    v01 = dy ? c : a;
-    v11 = dx ? (dy ? d : b) : (dy ? c : a);
+    v00 = float(g.w);
+    v10 = float(g.z);
+    v01 = float(g.x);
+    v11 = float(g.y);
 }
 
 // Depth range of the samples of a ray that can lie in a marked cell, from the
@@ -405,8 +406,6 @@ __device__ __forceinline__ bool march_step(RayMarch &S, const ViewParams &V, con
     }
     const int *Mm1 = G.m1;
     const int ix = int(S.U[0] >> 32), iy = int(S.U[1] >> 32), iz = int(S.U[2] >> 32);
-    const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]);
-    const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
     const float fx = float(uint32_t(S.U[0])) * 2.3283064365386963e-10f;
     const float fy = float(uint32_t(S.U[1])) * 2.3283064365386963e-10f;
     const float fz = float(uint32_t(S.U[2])) * 2.3283064365386963e-10f;
@@ -418,10 +417,14 @@ __device__ __forceinline__ bool march_step(RayMarch &S, const ViewParams &V, con
     }
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if constexpr (Tab::kGather) {
-        const bool dx = x1 != x0, dy = y1i != y0i;
-        gather_quad<T>(tab.tex, S.za, x0, y0i, dx, dy, v000, v100, v010, v110);
-        gather_quad<T>(tab.tex, S.zb, x0, y0i, dx, dy, v001, v101, v011, v111);
+        // a sample inside the box has its lower corner in [-1, M - 1] per axis;
+        // the clamp only keeps a rounding-level excursion inside its cell
+        const int gx = min(max(ix, -1), Mm1[0]), gy = min(max(iy, -1), Mm1[1]);
+        gather_quad<T>(tab.tex, S.za, gx, gy, v000, v100, v010, v110);
+        gather_quad<T>(tab.tex, S.zb, gx, gy, v001, v101, v011, v111);
     } else {
+        const int x0 = min(max(ix, 0), Mm1[0]), y0i = min(max(iy, 0), Mm1[1]);
+        const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
         const uint32_t pitch = G.pitch;
         const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
         v000 = texel(atlas, S.za + ya + x0);

@@ -3,10 +3,14 @@
 //
 // The atlas is copied into a 2D CUDA array made for texture gathers, with a
 // texture object that reads the stored integers as they are (point
-// sampling, coordinates in texels, clamped at the edges).  The batched
-// renderer then fetches the 2x2 in-slice corners of a sample with one gather
-// per slice; the gathered integers are the atlas values, so the
-// interpolation that follows is the same arithmetic on the same inputs.
+// sampling, coordinates in texels).  Each mx x my tile of the atlas sits in
+// a cell of (mx + 2) x (my + 2) texels whose one-texel border repeats the
+// tile's edge texels, so a gather whose 2x2 block reaches one texel past a
+// tile's edge reads the edge value, which is what clamping the corner index
+// to the level gives.  The batched renderer fetches the 2x2 in-slice corners
+// of a sample with one gather per slice and no clamping or selection; the
+// gathered integers are the atlas values, so the interpolation that follows
+// is the same arithmetic on the same inputs.
 #include "mctp_internal.cuh"
 
 namespace mctp {
@@ -16,42 +20,32 @@ int check_slicemap(const mctp_slicemap *sm);
 struct mctp_atlas_texture {
     cudaArray_t array = nullptr;
     cudaTextureObject_t tex = 0;
-    cudaSurfaceObject_t surf = 0;   // 0: the array takes no surface stores; updates use a 2D copy
-    int64_t width = 0, height = 0;  // texels
+    cudaSurfaceObject_t surf = 0;   // the update kernel's stores
+    int64_t width = 0, height = 0;  // texels, with the one-texel border of every cell
     int32_t dtype = 0;
+    int32_t mx = 0, my = 0, tiles_x = 0, tiles_y = 0;  // the level geometry at creation
 };
 
 namespace {
 
 constexpr int kSurfThreads = 256;
 
-// Row y of the atlas into the array.  Each warp moves 32 16-byte vectors:
-// coalesced loads into shared memory, then one surface store per texel with
-// the lanes on consecutive texels, so a warp's stores cover one contiguous
-// run of the row.  Rows hold a whole number of 16-byte vectors.
+// Row Y of the padded array, the cells of tile column blockIdx.x: texel
+// (X, Y) of cell (col, row) holds atlas texel (col mx + lx, row my + ly) with
+// lx = X - col (mx + 2) - 1 and ly likewise, both clamped to the tile.
+// Consecutive threads read and store consecutive texels.
 template <typename T>
-__global__ void __launch_bounds__(kSurfThreads) atlas_surface_kernel(const T *__restrict__ atlas, int32_t w,
-                                                                     cudaSurfaceObject_t surf)
+__global__ void __launch_bounds__(kSurfThreads) atlas_pad_kernel(const T *__restrict__ atlas, int64_t pitch,
+                                                                 int32_t mx, int32_t my, cudaSurfaceObject_t surf)
 {
-    constexpr int E = 16 / int(sizeof(T));
-    __shared__ __align__(16) uint4 stage[kSurfThreads];
-    const int y = blockIdx.y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint4 *row = reinterpret_cast<const uint4 *>(atlas + int64_t(y) * w);
-    const int nvec = w / E;
-    const int nchunks = (nvec + 31) / 32;
-    const T *mine = reinterpret_cast<const T *>(stage + warp * 32);
-    for (int c = blockIdx.x * (kSurfThreads / 32) + warp; c < nchunks; c += gridDim.x * (kSurfThreads / 32)) {
-        const int v = c * 32 + lane;
-        if (v < nvec) stage[warp * 32 + lane] = __ldg(row + v);
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int t = k * 32 + lane;
-            const int x = c * 32 * E + t;
-            if (x < w) surf2Dwrite<T>(mine[t], surf, x * int(sizeof(T)), y, cudaBoundaryModeZero);
-        }
-        __syncwarp();
+    const int Y = blockIdx.y, col = blockIdx.x;
+    const int row = Y / (my + 2);
+    const int ly = min(max(Y - row * (my + 2) - 1, 0), my - 1);
+    const T *src = atlas + (int64_t(row) * my + ly) * pitch + int64_t(col) * mx;
+    const int X0 = col * (mx + 2);
+    for (int i = threadIdx.x; i < mx + 2; i += blockDim.x) {
+        const int lx = min(max(i - 1, 0), mx - 1);
+        surf2Dwrite<T>(__ldg(src + lx), surf, (X0 + i) * int(sizeof(T)), Y, cudaBoundaryModeZero);
     }
 }
 
@@ -60,8 +54,8 @@ int texture_geometry(const mctp_slicemap *sm, int32_t level, int64_t &w, int64_t
     const int rc = mctp::check_slicemap(sm);
     if (rc != MCTP_OK) return rc;
     if (level < 0 || level >= sm->nlevels) return MCTP_EINVAL;
-    w = int64_t(sm->tiles_x[level]) * sm->dims[level][0];
-    h = int64_t(sm->tiles_y[level]) * sm->dims[level][1];
+    w = int64_t(sm->tiles_x[level]) * (sm->dims[level][0] + 2);
+    h = int64_t(sm->tiles_y[level]) * (sm->dims[level][1] + 2);
     return MCTP_OK;
 }
 
@@ -89,27 +83,25 @@ extern "C" int mctp_atlas_texture_create(const mctp_slicemap *sm, int32_t level,
     t->width = w;
     t->height = h;
     t->dtype = sm->dtype;
-    // surface stores for the update kernel where the array allows them, else 2D copies
-    const bool vec_rows = (w * mctp::elem_size(sm->dtype)) % 16 == 0;
-    if (!vec_rows ||
-        cudaMallocArray(&t->array, &cd, size_t(w), size_t(h), cudaArrayTextureGather | cudaArraySurfaceLoadStore) !=
-            cudaSuccess) {
+    t->mx = sm->dims[level][0];
+    t->my = sm->dims[level][1];
+    t->tiles_x = sm->tiles_x[level];
+    t->tiles_y = sm->tiles_y[level];
+    // the update kernel writes the padded cells with surface stores
+    if (cudaMallocArray(&t->array, &cd, size_t(w), size_t(h), cudaArrayTextureGather | cudaArraySurfaceLoadStore) !=
+        cudaSuccess) {
         cudaGetLastError();
-        t->array = nullptr;
-        if (cudaMallocArray(&t->array, &cd, size_t(w), size_t(h), cudaArrayTextureGather) != cudaSuccess) {
-            delete t;
-            return MCTP_ECUDA;
-        }
+        delete t;
+        return MCTP_ECUDA;
     }
     cudaResourceDesc rd{};
     rd.resType = cudaResourceTypeArray;
     rd.res.array.array = t->array;
-    unsigned int flags = 0;
-    if (cudaArrayGetInfo(nullptr, nullptr, &flags, t->array) == cudaSuccess && (flags & cudaArraySurfaceLoadStore)) {
-        if (cudaCreateSurfaceObject(&t->surf, &rd) != cudaSuccess) {
-            cudaGetLastError();
-            t->surf = 0;
-        }
+    if (cudaCreateSurfaceObject(&t->surf, &rd) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeArray(t->array);
+        delete t;
+        return MCTP_ECUDA;
     }
     cudaTextureDesc td{};
     td.addressMode[0] = cudaAddressModeClamp;
@@ -135,25 +127,20 @@ extern "C" int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slice
     int64_t w = 0, h = 0;
     const int rc = texture_geometry(sm, level, w, h);
     if (rc != MCTP_OK) return rc;
-    if (w != t->width || h != t->height || sm->dtype != t->dtype) return MCTP_EINVAL;
-    const size_t row = size_t(w) * size_t(mctp::elem_size(sm->dtype));
+    if (w != t->width || h != t->height || sm->dtype != t->dtype || sm->dims[level][0] != t->mx ||
+        sm->dims[level][1] != t->my || sm->tiles_x[level] != t->tiles_x || sm->tiles_y[level] != t->tiles_y)
+        return MCTP_EINVAL;
     cudaStream_t s = mctp::as_stream(stream);
-    if (t->surf && (reinterpret_cast<uintptr_t>(sm->atlas[level]) & 15) == 0) {
-        const int nchunks = int((row / 16 + 31) / 32);
-        const int per_block = kSurfThreads / 32;
-        const dim3 grid(unsigned((nchunks + per_block - 1) / per_block), unsigned(h));
-        if (sm->dtype == MCTP_U8)
-            atlas_surface_kernel<uint8_t>
-                <<<grid, kSurfThreads, 0, s>>>(static_cast<const uint8_t *>(sm->atlas[level]), int32_t(w), t->surf);
-        else
-            atlas_surface_kernel<uint16_t>
-                <<<grid, kSurfThreads, 0, s>>>(static_cast<const uint16_t *>(sm->atlas[level]), int32_t(w), t->surf);
-        return mctp::launch_status();
-    }
-    if (cudaMemcpy2DToArrayAsync(t->array, 0, 0, sm->atlas[level], row, row, size_t(h), cudaMemcpyDeviceToDevice,
-                                 s) != cudaSuccess)
-        return MCTP_ECUDA;
-    return MCTP_OK;
+    const dim3 grid(unsigned(sm->tiles_x[level]), unsigned(h));
+    const int64_t pitch = int64_t(sm->tiles_x[level]) * sm->dims[level][0];
+    if (sm->dtype == MCTP_U8)
+        atlas_pad_kernel<uint8_t><<<grid, kSurfThreads, 0, s>>>(static_cast<const uint8_t *>(sm->atlas[level]), pitch,
+                                                                 sm->dims[level][0], sm->dims[level][1], t->surf);
+    else
+        atlas_pad_kernel<uint16_t><<<grid, kSurfThreads, 0, s>>>(static_cast<const uint16_t *>(sm->atlas[level]),
+                                                                  pitch, sm->dims[level][0], sm->dims[level][1],
+                                                                  t->surf);
+    return mctp::launch_status();
 }
 
 extern "C" int mctp_atlas_texture_destroy(mctp_atlas_texture *t)

@@ -118,8 +118,9 @@ def test_texture_is_what_is_read(env):
 
 
 def test_texture_unaligned_atlas(env):
-    """Atlases that start 2 bytes past a 16-byte boundary update through the
-    2D copy; a batch of two slicemaps, both textured, renders as loads do."""
+    """Atlases that start 2 bytes past a 16-byte boundary fill their padded
+    textures as aligned ones do; a batch of two slicemaps, both textured,
+    renders as loads do."""
     mctp, oracle, phantom, dev = env
     a = _build(env, phantom.VolumeSpec(100, 90, 80, bits=12, seed=61, n_ell=4), [(64, 48, 40), (32, 24, 20)], 12)
     b = _build(env, phantom.VolumeSpec(70, 70, 70, bits=12, seed=62, n_ell=4), [(32, 32, 32)], 12)
