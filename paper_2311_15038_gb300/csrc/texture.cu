@@ -11,6 +11,8 @@
 // of a sample with one gather per slice and no clamping or selection; the
 // gathered integers are the atlas values, so the interpolation that follows
 // is the same arithmetic on the same inputs.
+#include <algorithm>
+
 #include "mctp_internal.cuh"
 
 namespace mctp {
@@ -28,24 +30,44 @@ struct mctp_atlas_texture {
 
 namespace {
 
-constexpr int kSurfThreads = 256;
+constexpr int kSurfThreads = 512;
 
-// Row Y of the padded array, the cells of tile column blockIdx.x: texel
-// (X, Y) of cell (col, row) holds atlas texel (col mx + lx, row my + ly) with
-// lx = X - col (mx + 2) - 1 and ly likewise, both clamped to the tile.
-// Consecutive threads read and store consecutive texels.
+// Row Y = blockIdx.x of the padded array.  The block stages its atlas row
+// (the row ly of tile row `row`) in shared memory, with 16-byte loads when
+// the row is 16-byte aligned, then writes the padded row: texel X of cell
+// (col, row) holds atlas texel (col mx + lx, ...) with lx = X - col (mx + 2) - 1
+// clamped to the tile.  Consecutive threads store consecutive texels; the
+// cell of X comes from a float estimate (X < 2^16 is exact) and one
+// correction.
 template <typename T>
 __global__ void __launch_bounds__(kSurfThreads) atlas_pad_kernel(const T *__restrict__ atlas, int64_t pitch,
-                                                                 int32_t mx, int32_t my, cudaSurfaceObject_t surf)
+                                                                 int32_t mx, int32_t my, int32_t width,
+                                                                 cudaSurfaceObject_t surf)
 {
-    const int Y = blockIdx.y, col = blockIdx.x;
+    extern __shared__ __align__(16) unsigned char sh_row_bytes[];
+    T *sh_row = reinterpret_cast<T *>(sh_row_bytes);
+    const int Y = blockIdx.x;
     const int row = Y / (my + 2);
     const int ly = min(max(Y - row * (my + 2) - 1, 0), my - 1);
-    const T *src = atlas + (int64_t(row) * my + ly) * pitch + int64_t(col) * mx;
-    const int X0 = col * (mx + 2);
-    for (int i = threadIdx.x; i < mx + 2; i += blockDim.x) {
-        const int lx = min(max(i - 1, 0), mx - 1);
-        surf2Dwrite<T>(__ldg(src + lx), surf, (X0 + i) * int(sizeof(T)), Y, cudaBoundaryModeZero);
+    const T *src = atlas + (int64_t(row) * my + ly) * pitch;
+    constexpr int E = 16 / int(sizeof(T));
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(src);
+        const int nvec = int(pitch / E);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) reinterpret_cast<uint4 *>(sh_row)[i] = __ldg(v + i);
+        for (int i = nvec * E + threadIdx.x; i < pitch; i += blockDim.x) sh_row[i] = __ldg(src + i);
+    } else {
+        for (int i = threadIdx.x; i < pitch; i += blockDim.x) sh_row[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    const int cw = mx + 2;
+    const float inv = 1.0f / float(cw);
+    for (int X = threadIdx.x; X < width; X += blockDim.x) {
+        int col = int(float(X) * inv);
+        if (col * cw > X) --col;
+        else if ((col + 1) * cw <= X) ++col;
+        const int lx = min(max(X - col * cw - 1, 0), mx - 1);
+        surf2Dwrite<T>(sh_row[col * mx + lx], surf, X * int(sizeof(T)), Y, cudaBoundaryModeZero);
     }
 }
 
@@ -131,15 +153,22 @@ extern "C" int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slice
         sm->dims[level][1] != t->my || sm->tiles_x[level] != t->tiles_x || sm->tiles_y[level] != t->tiles_y)
         return MCTP_EINVAL;
     cudaStream_t s = mctp::as_stream(stream);
-    const dim3 grid(unsigned(sm->tiles_x[level]), unsigned(h));
     const int64_t pitch = int64_t(sm->tiles_x[level]) * sm->dims[level][0];
+    const size_t smem = size_t(pitch) * size_t(mctp::elem_size(sm->dtype));
+    auto kern = sm->dtype == MCTP_U8 ? reinterpret_cast<const void *>(atlas_pad_kernel<uint8_t>)
+                                     : reinterpret_cast<const void *>(atlas_pad_kernel<uint16_t>);
+    if (smem > 200 * 1024) return MCTP_ESIZE;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return MCTP_ECUDA;
     if (sm->dtype == MCTP_U8)
-        atlas_pad_kernel<uint8_t><<<grid, kSurfThreads, 0, s>>>(static_cast<const uint8_t *>(sm->atlas[level]), pitch,
-                                                                 sm->dims[level][0], sm->dims[level][1], t->surf);
+        atlas_pad_kernel<uint8_t><<<unsigned(h), kSurfThreads, smem, s>>>(
+            static_cast<const uint8_t *>(sm->atlas[level]), pitch, sm->dims[level][0], sm->dims[level][1], int32_t(w),
+            t->surf);
     else
-        atlas_pad_kernel<uint16_t><<<grid, kSurfThreads, 0, s>>>(static_cast<const uint16_t *>(sm->atlas[level]),
-                                                                  pitch, sm->dims[level][0], sm->dims[level][1],
-                                                                  t->surf);
+        atlas_pad_kernel<uint16_t><<<unsigned(h), kSurfThreads, smem, s>>>(
+            static_cast<const uint16_t *>(sm->atlas[level]), pitch, sm->dims[level][0], sm->dims[level][1],
+            int32_t(w), t->surf);
     return mctp::launch_status();
 }
 
