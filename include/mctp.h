@@ -47,6 +47,7 @@ extern "C" {
 #define MCTP_EUNSUPPORTED (-2) /* dtype / bits / mode not supported */
 #define MCTP_ESIZE (-3)        /* atlas tile grid too small, too many views */
 #define MCTP_ECUDA (-4)        /* a CUDA launch or copy failed */
+#define MCTP_ECANCELED (-6)    /* serving: the request was cancelled before its launch */
 
 /* voxel types */
 #define MCTP_U8 1
@@ -406,6 +407,16 @@ int mctp_server_submit(mctp_server *server, const mctp_view *view, int32_t slice
 int mctp_server_poll(mctp_server *server, mctp_serve_result *results, int32_t max_results, int32_t *count);
 /* Return a finished request's image memory to the arena. */
 int mctp_server_release(mctp_server *server, uint64_t ticket);
+/* Cancel a request that has not been launched yet: it leaves the queue (and
+ * returns its image memory when it was admitted) and is reported by poll with
+ * status MCTP_ECANCELED, after which it is released like any other.  A request
+ * already launched, finished or unknown is not cancelled (MCTP_EINVAL). */
+int mctp_server_cancel(mctp_server *server, uint64_t ticket);
+/* Host-side fault injection for tests: the next `n` launches of the server
+ * fail as a failed kernel launch would (nothing is enqueued; their requests
+ * finish with status MCTP_ECUDA), after which the server carries on.  No GPU
+ * fault is made. */
+int mctp_server_inject_launch_failures(mctp_server *server, int32_t n);
 /* Samples marched, launches made and the image heap's high-water mark (bytes). */
 int mctp_server_stats(mctp_server *server, uint64_t *samples, uint64_t *launches, uint64_t *arena_high_water);
 /* Wait for launches in flight, drop requests not yet launched, free the server. */

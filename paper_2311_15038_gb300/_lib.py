@@ -12,6 +12,7 @@ MCTP_EUNSUPPORTED = -2
 MCTP_ESIZE = -3
 MCTP_BATCH_COUNT_EVALUATED = 1
 MCTP_ECUDA = -4
+MCTP_ECANCELED = -6
 
 MCTP_U8 = 1
 MCTP_U16 = 2
@@ -92,6 +93,8 @@ EXPORTS = {
                            ctypes.c_int),
     "mctp_server_poll": ([C_VP, ctypes.POINTER(ServeResult), C_I32, ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_server_release": ([C_VP, ctypes.c_uint64], ctypes.c_int),
+    "mctp_server_cancel": ([C_VP, ctypes.c_uint64], ctypes.c_int),
+    "mctp_server_inject_launch_failures": ([C_VP, C_I32], ctypes.c_int),
     "mctp_server_stats": ([C_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "mctp_server_destroy": ([C_VP], ctypes.c_int),

@@ -12,6 +12,7 @@ extern "C" const char *mctp_status_string(int code)
     case MCTP_EUNSUPPORTED: return "unsupported dtype, bit depth, mode or size";
     case MCTP_ESIZE: return "size limit exceeded (atlas tile grid, view size)";
     case MCTP_ECUDA: return "CUDA launch or copy failed";
+    case MCTP_ECANCELED: return "request cancelled before its launch";
     default: return "unknown status";
     }
 }

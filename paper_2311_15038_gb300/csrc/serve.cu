@@ -103,6 +103,7 @@ struct Request {
     int32_t sm = 0, lut = 0;
     int state = kQueued;
     int status = MCTP_OK;
+    bool has_img = false;  // its image memory is taken from the heap
     size_t img_off = 0, img_bytes = 0;
     double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
 };
@@ -140,6 +141,7 @@ struct mctp_server {
     mctp::Arena heap;
     std::vector<mctp::Slot> slots;
     uint64_t samples_total = 0, launches = 0;
+    int32_t fail_launches = 0;  // fault injection: launches still to fail
     std::thread worker;
 
     void run();
@@ -167,7 +169,17 @@ bool mctp_server::launch(Slot &slot, std::vector<uint64_t> &batch)
         }
     }
     int rc;
-    if (params.mode == MCTP_SERVE_PER_VIEW) {
+    bool inject = false;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (fail_launches > 0) {
+            --fail_launches;
+            inject = true;
+        }
+    }
+    if (inject) {
+        rc = MCTP_ECUDA;  // as a failed launch: nothing is enqueued
+    } else if (params.mode == MCTP_SERVE_PER_VIEW) {
         rc = mctp_render_views(&sms[vsm[0]], &v[0], 1, luts + size_t(vlut[0]) * nlut * 4, nlut, alpha_stop,
                                reinterpret_cast<float *>(arena) + off[0], slot.d_samples, slot.stream);
     } else {
@@ -237,6 +249,7 @@ void mctp_server::run()
             size_t off = 0;
             if (!heap.alloc(r.img_bytes, &off)) break;
             r.img_off = off;
+            r.has_img = true;
             r.state = mctp::kAdmitted;
             r.t_admit = mctp::now_s();
             admitted.push_back(queued.front());
@@ -377,7 +390,7 @@ extern "C" int mctp_server_poll(mctp_server *S, mctp_serve_result *results, int3
         o.ticket = tk;
         o.status = r.status;
         o.reserved = 0;
-        o.image = reinterpret_cast<float *>(S->arena + r.img_off);
+        o.image = r.has_img ? reinterpret_cast<float *>(S->arena + r.img_off) : nullptr;
         o.t_submit = r.t_submit;
         o.t_admit = r.t_admit;
         o.t_launch = r.t_launch;
@@ -394,10 +407,45 @@ extern "C" int mctp_server_release(mctp_server *S, uint64_t ticket)
         std::lock_guard<std::mutex> lock(S->mu);
         auto it = S->reqs.find(ticket);
         if (it == S->reqs.end() || it->second.state != mctp::kDone) return MCTP_EINVAL;
-        S->heap.release(it->second.img_off, it->second.img_bytes);  // done implies admitted
+        if (it->second.has_img) S->heap.release(it->second.img_off, it->second.img_bytes);
         S->reqs.erase(it);
     }
     S->cv.notify_one();
+    return MCTP_OK;
+}
+
+extern "C" int mctp_server_cancel(mctp_server *S, uint64_t ticket)
+{
+    if (!S) return MCTP_EINVAL;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return MCTP_EINVAL;
+        Request &r = it->second;
+        std::deque<uint64_t> *q = r.state == mctp::kQueued ? &S->queued
+                                  : r.state == mctp::kAdmitted ? &S->admitted : nullptr;
+        if (!q) return MCTP_EINVAL;  // launched or finished: too late
+        auto at = std::find(q->begin(), q->end(), ticket);
+        if (at == q->end()) return MCTP_EINVAL;  // being launched by the server thread right now
+        q->erase(at);
+        if (r.has_img) {
+            S->heap.release(r.img_off, r.img_bytes);
+            r.has_img = false;
+        }
+        r.state = mctp::kDone;
+        r.status = MCTP_ECANCELED;
+        r.t_done = mctp::now_s();
+        S->finished.push_back(ticket);
+    }
+    S->cv.notify_one();
+    return MCTP_OK;
+}
+
+extern "C" int mctp_server_inject_launch_failures(mctp_server *S, int32_t n)
+{
+    if (!S || n < 0) return MCTP_EINVAL;
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->fail_launches = n;
     return MCTP_OK;
 }
 

@@ -147,6 +147,41 @@ class Fitter:
         adam_step(self.vol, self.g_vol, self.m_vol, self.v_vol, self.t, self.lr_vol, lo=0.0, hi=1.0, stream=s)
         adam_step(self.lut, self.g_lut, self.m_lut, self.v_lut, self.t, self.lr_lut, lo=0.0, hi=1.0, stream=s)
 
+    _STATE = ("vol", "lut", "m_vol", "v_vol", "m_lut", "v_lut")
+
+    def state_dict(self) -> dict:
+        """Everything a resumed fit needs: the reduced volume, the transfer
+        function, both Adam moment pairs, the step count and the settings
+        (copies on the host; the caller saves them, e.g. with torch.save).
+        Waits for the fit's queued work first."""
+        if self.stream is not None:
+            self.stream.synchronize()
+        elif self.vol.is_cuda:
+            torch.cuda.synchronize(self.vol.device)
+        out = {k: getattr(self, k).detach().cpu().clone() for k in self._STATE}
+        out.update(t=self.t, lr_vol=self.lr_vol, lr_lut=self.lr_lut, alpha_stop=self.alpha_stop,
+                   src_dims=tuple(int(v) for v in self.src_dims),
+                   views=[(v.azimuth_deg, v.elevation_deg, v.width, v.height, v.level, v.step) for v in self.views])
+        return out
+
+    def load_state_dict(self, state: dict) -> None:
+        """Continue a fit from state_dict(): the same views, source and shapes
+        are required (checked), after which the next step() is the step the
+        saved fit would have taken."""
+        views = [(v.azimuth_deg, v.elevation_deg, v.width, v.height, v.level, v.step) for v in self.views]
+        if [tuple(v) for v in state["views"]] != views or tuple(state["src_dims"]) != tuple(self.src_dims):
+            raise ValueError("the saved fit has other views or another source volume")
+        for k in self._STATE:
+            dst = getattr(self, k)
+            src = state[k]
+            if tuple(src.shape) != tuple(dst.shape) or src.dtype != dst.dtype:
+                raise ValueError(f"saved {k} has shape {tuple(src.shape)} / {src.dtype}, "
+                                 f"expected {tuple(dst.shape)} / {dst.dtype}")
+            dst.copy_(src.to(dst.device))
+        self.t = int(state["t"])
+        self.lr_vol, self.lr_lut = float(state["lr_vol"]), float(state["lr_lut"])
+        self.alpha_stop = float(state["alpha_stop"])
+
     def evaluate(self) -> float:
         """Loss of the current parameters (synchronises)."""
         render_dense(self.vol, self.lut, self.views, self.src_dims, self.alpha_stop, self.images, self.samples,

@@ -89,6 +89,19 @@ class Server:
         _lib.check(self._lib.mctp_server_release(self._h, ticket), "mctp_server_release")
         self._views.pop(ticket, None)
 
+    def cancel(self, ticket: int) -> bool:
+        """Cancel a request not launched yet; True if it was (poll then reports
+        it with status MCTP_ECANCELED), False if it was already launched or done."""
+        rc = self._lib.mctp_server_cancel(self._h, ticket)
+        if rc not in (_lib.MCTP_OK, _lib.MCTP_EINVAL):
+            _lib.check(rc, "mctp_server_cancel")
+        return rc == _lib.MCTP_OK
+
+    def inject_launch_failures(self, n: int) -> None:
+        """Test hook: the next n launches fail on the host as a failed kernel
+        launch would (no GPU fault); their requests finish with MCTP_ECUDA."""
+        _lib.check(self._lib.mctp_server_inject_launch_failures(self._h, n), "mctp_server_inject_launch_failures")
+
     def stats(self) -> dict:
         s, l, h = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _lib.check(self._lib.mctp_server_stats(self._h, ctypes.byref(s), ctypes.byref(l), ctypes.byref(h)),

@@ -316,3 +316,38 @@ def test_autograd_and_small_fit(env):
     l1 = f.evaluate()
     print(f"small fit: loss {l0:.4e} -> {l1:.4e}")
     assert l1 < 0.5 * l0
+
+
+def test_fit_resumes_from_checkpoint(env, tmp_path):
+    """A fit stopped after 6 steps, saved with torch.save and resumed in a new
+    fitter continues as the uninterrupted fit does: after 6 more steps both
+    reach the same loss and parameters (within the float-atomic summation
+    order of the adjoint), and the resumed step count is 12."""
+    mctp, diff, oracle, phantom, dev = env
+    vol, lut = _case(phantom, 6, (16, 16, 16))
+    src = (48, 48, 48)
+    views = [mctp.View(40.0 * k, 15.0 if k % 2 else -15.0, 20, 20, 0, 0.5) for k in range(4)]
+    target, _ = diff.render_dense(torch.from_numpy(vol).to(dev), torch.from_numpy(lut).to(dev), views, src, 0.99)
+    total = sum(v.width * v.height * 4 for v in views)
+    start = torch.from_numpy(np.clip(vol * 0.7 + 0.1, 0, 1).astype(np.float32)).to(dev)
+
+    def fitter():
+        return diff.Fitter(start, torch.from_numpy(lut).to(dev), views, src, target[:total], 0.99, 2e-2, 5e-3)
+    whole = fitter()
+    for _ in range(6):
+        whole.step()
+    path = tmp_path / "fit.pt"
+    torch.save(whole.state_dict(), path)
+    for _ in range(6):
+        whole.step()
+    resumed = fitter()
+    resumed.load_state_dict(torch.load(path))
+    for _ in range(6):
+        resumed.step()
+    torch.cuda.synchronize()
+    assert resumed.t == whole.t == 12
+    lw, lr = whole.evaluate(), resumed.evaluate()
+    print(f"loss after 12 steps: uninterrupted {lw:.6e}, resumed {lr:.6e}")
+    assert abs(lw - lr) <= 1e-4 * lw
+    assert torch.allclose(whole.vol, resumed.vol, rtol=0, atol=1e-4)
+    assert torch.allclose(whole.lut, resumed.lut, rtol=0, atol=1e-4)

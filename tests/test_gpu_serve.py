@@ -144,3 +144,98 @@ def test_served_with_textures_and_depth_bounds(env):
             total += smp
             assert torch.equal(got[i][1], ref), f"request {i} of the {batch}-view server differs"
         assert st["samples"] == total
+
+
+def _drain(srv, n, timeout=60.0):
+    """Poll until n requests have finished; returns {ticket: Finished}."""
+    got = {}
+    t0 = time.time()
+    while len(got) < n:
+        for f in srv.poll():
+            got[f.ticket] = f
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.0005)
+    return got
+
+
+def test_cancelled_requests_leave_the_queue(env):
+    """Requests waiting for memory (a 3 MiB arena whose image heap holds at
+    most two 256^2 images) are cancelled: they finish with MCTP_ECANCELED and no image,
+    take no launch, and the requests not cancelled still equal rendering their
+    views alone; a finished or unknown ticket is not cancellable."""
+    mctp, serve, sms, luts, dev = env
+    from paper_2311_15038_gb300 import _lib
+    v = mctp.View(20.0, 10.0, 256, 256, 0, 0.5)
+    reqs = [(v, i % len(sms), i % 8) for i in range(8)]
+    with serve.Server(sms, luts, 3 << 20, "batched", 8, 1) as srv:
+        tickets = [srv.submit(*r) for r in reqs]
+        cancelled = [t for t in tickets[2:7] if srv.cancel(t)]
+        assert len(cancelled) >= 3  # the first two may already be admitted or launched
+        got = {}
+        t0 = time.time()
+        while len(got) < len(tickets):
+            for f in srv.poll():
+                if f.status == 0:
+                    img = srv.image(f).clone()
+                    srv.release(f.ticket)
+                    got[f.ticket] = (f, img)
+                else:
+                    got[f.ticket] = (f, None)
+                    srv.release(f.ticket)
+            assert time.time() - t0 < 60.0
+            time.sleep(0.0005)
+        for t in cancelled:
+            f, img = got[t]
+            assert f.status == _lib.MCTP_ECANCELED and f.image_ptr == 0 and img is None
+        for t, r in zip(tickets, reqs):
+            if t in cancelled:
+                continue
+            f, img = got[t]
+            assert f.status == 0
+            ref, _ = _alone(mctp, sms, luts, r)
+            assert torch.equal(img, ref)
+        assert srv.stats()["launches"] <= len(tickets) - len(cancelled)
+        assert not srv.cancel(tickets[0])        # finished and released
+        assert not srv.cancel(123456789)         # unknown
+
+
+def test_injected_launch_failures(env):
+    """Host-side fault injection: the next two launches fail as a failed
+    kernel launch would; their requests finish with MCTP_ECUDA, nothing is
+    left in flight, and the server serves the following requests correctly."""
+    mctp, serve, sms, luts, dev = env
+    from paper_2311_15038_gb300 import _lib
+    reqs = _requests(mctp, sms, 12, seed=21)
+    with serve.Server(sms, luts, 64 << 20, "per_view", 1, 1) as srv:
+        srv.inject_launch_failures(2)
+        first = [srv.submit(*r) for r in reqs[:4]]
+        done = _drain(srv, 4)
+        status = [done[t].status for t in first]
+        assert status.count(_lib.MCTP_ECUDA) == 2 and status.count(0) == 2
+        for t in first:
+            srv.release(t)
+        got = _serve_all(srv, reqs[4:])
+        for i, (f, img) in got.items():
+            ref, _ = _alone(mctp, sms, luts, reqs[4 + i])
+            assert torch.equal(img, ref)
+
+
+def test_slow_producer_and_malformed_requests(env):
+    """Requests that trickle in one by one (the server idles between them)
+    each finish alone and correct; malformed requests (bad slicemap or LUT
+    index, a level the slicemap lacks, a zero-sized view) are refused at
+    submit and leave nothing behind."""
+    mctp, serve, sms, luts, dev = env
+    reqs = _requests(mctp, sms, 5, seed=33)
+    with serve.Server(sms, luts, 64 << 20, "batched", 16, 2) as srv:
+        for r in reqs:
+            got = _serve_all(srv, [r])
+            ref, _ = _alone(mctp, sms, luts, r)
+            assert torch.equal(got[0][1], ref)
+            time.sleep(0.01)
+        v = mctp.View(0.0, 0.0, 32, 32, 0, 0.5)
+        for bad in [(v, len(sms), 0), (v, 0, 99), (mctp.View(0.0, 0.0, 32, 32, 5, 0.5), 1, 0),
+                    (mctp.View(0.0, 0.0, 0, 32, 0, 0.5), 0, 0)]:
+            with pytest.raises(mctp.MctpError):
+                srv.submit(*bad)
+        assert srv.poll() == []
