@@ -27,6 +27,8 @@
 // separate 2x2x2 kernel, and max grids are built by maxgrid_kernel.
 // When the keep table is a step (keep[b] = b >= T, as Otsu, ITS and explicit
 // thresholds produce) the per-voxel table lookup becomes one comparison.
+// A single u8 level from rows of at most 1024 bytes (many small volumes) takes
+// a warp-per-row kernel instead (slicemap_rows_u8_kernel below).
 #include <algorithm>
 
 #include "slicemap_common.cuh"
@@ -339,6 +341,193 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
     }
 }
 
+// ---- level 0 alone, u8 source rows of at most 1024 bytes (many small volumes)
+//
+// One warp per level-0 row (z, y) at a time, persistent warps, no CTA barrier
+// in the loop.  Lane l owns source columns [32 l, 32 l + 32): for each source
+// row of the footprint it loads the three aligned 16-byte chunks around its 32
+// bytes (any row alignment), funnel-shifts them into place and adds the bytes
+// into packed 16-bit column sums (kept values only); the warp then writes its
+// column sums to its own shared row and each lane takes output columns x =
+// lane, lane + 32, ... : the sum over the x footprint, divided and rounded.
+// The x, y and z footprint tables and the keep table are set up once per
+// block.
+constexpr int kRowsWarps = 8;
+constexpr int kRowsMaxCols = 1024;                             // source row bytes the kernel takes
+constexpr int kRowsMaxYZ = 4096;                               // level rows / slices the tables take
+constexpr int kRowsColsPad = kRowsMaxCols + kRowsMaxCols / 4;  // u16 per warp row: 8 of padding per 32
+
+struct RowsArgs {
+    const uint8_t *vol;
+    int64_t nx, ny, nz;
+    int32_t mx, my, mz;
+    uint8_t *atlas;
+    int32_t tiles_x;
+    int64_t pitch;
+    const uint8_t *keep;
+    int32_t nbins, shift;
+    uint32_t limit;
+};
+
+// The 32 bytes at p (lane-uniform p & 15) from the aligned chunks c0, c0 + 16,
+// c0 + 32; a chunk that holds no byte of [row, end) is not loaded (its bytes
+// form columns past the row, which no output reads).
+__device__ __forceinline__ void load_lane32(const char *p, const char *end, uint4 &lo, uint4 &hi)
+{
+    const uint32_t m = uint32_t(reinterpret_cast<uintptr_t>(p) & 15u);
+    const uint4 *c = reinterpret_cast<const uint4 *>(p - m);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 q0 = __ldg(c);
+    const uint4 q1 = reinterpret_cast<const char *>(c + 1) < end ? __ldg(c + 1) : z;
+    if (m == 0) {
+        lo = q0;
+        hi = q1;
+        return;
+    }
+    const uint4 q2 = reinterpret_cast<const char *>(c + 2) < end ? __ldg(c + 2) : z;
+    const uint32_t W[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+    const uint32_t sh = (m & 3u) * 8u;
+    uint32_t o[8];
+    switch (m >> 2) {
+    case 0:
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = __funnelshift_r(W[k], W[k + 1], sh);
+        break;
+    case 1:
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = __funnelshift_r(W[k + 1], W[k + 2], sh);
+        break;
+    case 2:
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = __funnelshift_r(W[k + 2], W[k + 3], sh);
+        break;
+    default:
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = __funnelshift_r(W[k + 3], W[k + 4], sh);
+        break;
+    }
+    lo = make_uint4(o[0], o[1], o[2], o[3]);
+    hi = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+// 16 bytes into packed even/odd column sums for a general keep table (mode 1).
+__device__ __forceinline__ void add_vector_u8_lut(const uint4 &q, uint32_t *acc, const uint8_t *lut, int shift)
+{
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t b[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t v = (w[k] >> (8 * j)) & 0xffu;
+            b[j] = lut[v >> shift] ? v : 0u;
+        }
+        acc[2 * k] += b[0] | (b[2] << 16);
+        acc[2 * k + 1] += b[1] | (b[3] << 16);
+    }
+}
+
+// floor((sum + cnt / 2) / cnt) for a quotient of at most a few hundred: a float
+// estimate and one correction step each way.
+__device__ __forceinline__ uint32_t div_round(uint32_t sum, uint32_t cnt, float rcp)
+{
+    const uint32_t n = sum + cnt / 2u;
+    uint32_t q = __float2uint_rz(__fmul_rn(float(n), rcp));
+    if ((q + 1u) * cnt <= n) ++q;
+    else if (q * cnt > n) --q;
+    return q;
+}
+
+template <int kMode>
+__device__ __forceinline__ void rows_accumulate(const RowsArgs &a, const uint8_t *lut, uint32_t k_fast, int zlo,
+                                                int ylo, int wy, int R, int lane, uint32_t acc[16])
+{
+    const int64_t nx = a.nx;
+    const char *rs = reinterpret_cast<const char *>(a.vol) + (int64_t(zlo) * a.ny + ylo) * nx;
+    const int64_t slice_jump = (a.ny - wy + 1) * nx;
+    int yi = 0;
+    for (int r = 0; r < R; r += 2) {
+        uint4 q[4];
+        const char *r1 = rs;
+        if (++yi == wy) { yi = 0; rs += slice_jump; } else { rs += nx; }
+        load_lane32(r1 + 32 * lane, r1 + nx, q[0], q[1]);
+        if (r + 1 < R) {
+            const char *r2 = rs;
+            if (++yi == wy) { yi = 0; rs += slice_jump; } else { rs += nx; }
+            load_lane32(r2 + 32 * lane, r2 + nx, q[2], q[3]);
+        } else {
+            q[2] = q[3] = make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (kMode == 1) add_vector_u8_lut(q[u], acc + 8 * (u & 1), lut, a.shift);
+            else add_vector_u8_packed<kMode>(q[u], acc + 8 * (u & 1), k_fast);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(const __grid_constant__ RowsArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem_rows[];
+    int32_t *xb = reinterpret_cast<int32_t *>(smem_rows);  // mx + 1
+    int32_t *yb = xb + a.mx + 1;                           // my + 1
+    int32_t *zb = yb + a.my + 1;                           // mz + 1
+    const int ntab = a.mx + a.my + a.mz + 3;
+    uint16_t *cols = reinterpret_cast<uint16_t *>(smem_rows + ((size_t(ntab) * 4 + 15) / 16) * 16);
+    uint8_t *lut = reinterpret_cast<uint8_t *>(cols + kRowsWarps * kRowsColsPad);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i <= a.mx; i += blockDim.x) xb[i] = int32_t((int64_t(i) * a.nx) / a.mx);
+    for (int i = threadIdx.x; i <= a.my; i += blockDim.x) yb[i] = int32_t((int64_t(i) * a.ny) / a.my);
+    for (int i = threadIdx.x; i <= a.mz; i += blockDim.x) zb[i] = int32_t((int64_t(i) * a.nz) / a.mz);
+    __shared__ int sh_keep[2];
+    uint32_t lo = 0;
+    const int mode = load_keep_table(a.keep, a.nbins, a.shift, a.limit, lut, sh_keep, int(threadIdx.x),
+                                     int(blockDim.x), &lo, [] { __syncthreads(); });
+    __syncthreads();
+    const uint32_t k_fast = (0x8000u - lo) * 0x00010001u;
+    uint16_t *mine = cols + warp * kRowsColsPad;
+    const int64_t nrows = int64_t(a.mz) * a.my;
+    const int64_t nwarps = int64_t(gridDim.x) * kRowsWarps;
+    const bool active = 32 * lane < a.nx;
+    for (int64_t row = int64_t(blockIdx.x) * kRowsWarps + warp; row < nrows; row += nwarps) {
+        const int z = int(row / a.my), y = int(row - int64_t(z) * a.my);
+        const int zlo = zb[z], ylo = yb[y];
+        const int wy = yb[y + 1] - ylo, R = (zb[z + 1] - zlo) * wy;
+        uint32_t acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = 0u;
+        if (active) {
+            if (mode == 0) rows_accumulate<0>(a, lut, k_fast, zlo, ylo, wy, R, lane, acc);
+            else if (mode == 1) rows_accumulate<1>(a, lut, k_fast, zlo, ylo, wy, R, lane, acc);
+            else rows_accumulate<2>(a, lut, k_fast, zlo, ylo, wy, R, lane, acc);
+        }
+        // column sums of columns 32 lane + 16 h + 4 k + j as u16, 8 of padding per 32 columns
+        uint4 *dst = reinterpret_cast<uint4 *>(mine + 40 * lane);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t w[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t ev = acc[8 * h + 2 * k], od = acc[8 * h + 2 * k + 1];
+                asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(w[2 * k]) : "r"(ev), "r"(od));
+                asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w[2 * k + 1]) : "r"(ev), "r"(od));
+            }
+            dst[2 * h] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[2 * h + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        __syncwarp();
+        uint8_t *out = atlas_ptr(a.atlas, a.pitch, a.tiles_x, a.mx, a.my, 0, y, z);
+        for (int x = lane; x < a.mx; x += 32) {
+            const int c0 = xb[x], c1 = xb[x + 1];
+            uint32_t sum = 0;
+            for (int c = c0; c < c1; ++c) sum += mine[c + (c >> 5) * 8];
+            const uint32_t cnt = uint32_t(c1 - c0) * uint32_t(R);
+            out[x] = uint8_t(div_round(sum, cnt, 1.0f / float(cnt)));
+        }
+        __syncwarp();
+    }
+}
+
 // Level k+1 from level k, atlas to atlas: exact 2x2x2 mean, rounded half up.
 template <typename T>
 __global__ void __launch_bounds__(256) halve_kernel(const T *__restrict__ src, int64_t src_pitch, int src_tx, int mx,
@@ -438,7 +627,40 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
 {
     int rc = MCTP_OK;
     int done_levels = 0;   // levels 1..done_levels written by the level-0 kernel
-    {
+    const int64_t rmax_all = ((d->ny + sm->dims[0][1] - 1) / sm->dims[0][1]) *
+                             ((d->nz + sm->dims[0][2] - 1) / sm->dims[0][2]);
+    if (sizeof(T) == 1 && sm->nlevels == 1 && d->nx <= kRowsMaxCols && sm->dims[0][1] <= kRowsMaxYZ &&
+        sm->dims[0][2] <= kRowsMaxYZ && rmax_all * 255 < 65536) {
+        // a single u8 level with short rows: the warp-per-row kernel
+        RowsArgs a{};
+        a.vol = reinterpret_cast<const uint8_t *>(vol);
+        a.nx = d->nx; a.ny = d->ny; a.nz = d->nz;
+        a.mx = sm->dims[0][0]; a.my = sm->dims[0][1]; a.mz = sm->dims[0][2];
+        a.atlas = static_cast<uint8_t *>(sm->atlas[0]);
+        a.tiles_x = sm->tiles_x[0];
+        a.pitch = int64_t(sm->tiles_x[0]) * sm->dims[0][0];
+        a.keep = keep;
+        a.nbins = keep ? nbins : 0;
+        a.shift = keep ? bin_shift(d->bits, nbins) : 0;
+        a.limit = 1u << d->bits;
+        const size_t smem = ((size_t(a.mx + a.my + a.mz + 3) * 4 + 15) / 16) * 16 +
+                            size_t(kRowsWarps) * kRowsColsPad * 2 + (keep ? size_t(nbins) : 0);
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(slicemap_rows_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+                cudaSuccess)
+            return MCTP_ECUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slicemap_rows_u8_kernel, kRowsWarps * 32, smem) !=
+            cudaSuccess)
+            return MCTP_ECUDA;
+        per_sm = std::max(per_sm, 1);
+        const int64_t rows = int64_t(a.mz) * a.my;
+        const int64_t grid = std::min<int64_t>((rows + kRowsWarps - 1) / kRowsWarps, int64_t(per_sm) * num_sms());
+        slicemap_rows_u8_kernel<<<unsigned(grid), kRowsWarps * 32, smem, s>>>(a);
+        rc = launch_status();
+        if (rc != MCTP_OK) return rc;
+        done_levels = sm->nlevels;  // nothing left for the other kernels
+    } else {
         const int fused = std::min(sm->nlevels - 1, kMaxFused);
         L0Args<T> a{};
         a.vol = vol;

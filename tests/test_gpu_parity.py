@@ -276,6 +276,36 @@ def test_slicemap_single_level_groups(env, shape, dims, bits, mode):
     _check_atlases(sm, oracle.slicemap(vol, bits, [dims], keep_ref), oracle)
 
 
+@pytest.mark.parametrize("shape,dims,mode,offset", [
+    ((40, 36, 1024), (256, 18, 20), "otsu", 0),      # the longest rows the warp-per-row kernel takes
+    ((40, 36, 1023), (300, 12, 13), "topslab", 1),   # odd rows, unaligned base, table lookup
+    ((64, 64, 100), (50, 4, 4), "its", 0),           # 16 x 16 footprints: 256 rows per level-0 row
+    ((9, 7, 1), (1, 3, 2), None, 0),                 # one-byte rows
+    ((23, 29, 31), (31, 29, 23), None, 3),           # identity, rows shorter than a lane's 32 bytes
+    ((50, 41, 545), (128, 40, 25), "otsu", 5),       # uneven x footprints straddling lanes
+])
+def test_slicemap_u8_rows_kernel(env, shape, dims, mode, offset):
+    """Single u8 levels with rows of at most 1024 bytes (the warp-per-row
+    kernel): bit-exact against the oracle for every keep-table kind, any
+    row alignment (the volume starts `offset` bytes into its buffer), footprints
+    from 1 to 16 voxels per axis."""
+    mctp, oracle, phantom, dev = env
+    nz, ny, nx = shape
+    vol = phantom.generate_cpu(phantom.VolumeSpec(nx, ny, nz, bits=8, seed=nx + 3 * nz, n_ell=5))
+    keep_ref = None
+    if mode == "topslab":
+        keep_ref = oracle.keep_topslab(oracle.histogram(vol, 8, 256, 0, 3)[0], 1)
+    elif mode is not None:
+        h, _ = oracle.histogram(vol, 8, 256)
+        keep_ref = oracle.keep_threshold(256, oracle.otsu(h)[0] if mode == "otsu" else oracle.its(h)[0])
+    buf = torch.zeros(vol.size + 64, dtype=torch.uint8, device=dev)
+    g = buf[offset:offset + vol.size].view(nz, ny, nx)
+    g.copy_(torch.from_numpy(vol))
+    sm = mctp.Slicemap.allocate((nx, ny, nz), dims, 1, torch.uint8, 8, dev)
+    mctp.build_slicemap(g, 8, sm, up(keep_ref, dev) if keep_ref is not None else None)
+    _check_atlases(sm, oracle.slicemap(vol, 8, [dims], keep_ref), oracle)
+
+
 def test_slicemap_custom_tiles(env):
     mctp, oracle, phantom, dev = env
     vol = phantom.generate_cpu(phantom.VolumeSpec(64, 48, 52, bits=8, seed=12, n_ell=4))
