@@ -537,6 +537,28 @@ size_t mctp_maxgrid_bytes(int32_t mx, int32_t my, int32_t mz);
 /* Static string for a status code. */
 const char *mctp_status_string(int code);
 
+/*
+ * Checked build.  The build can make a second library, compiled with
+ * MCTP_CHECKED, in which the histogram, filter, slicemap and render kernels
+ * test their main indices (histogram bins, keep-table entries, atlas elements
+ * written and read, transfer-function entries, slice offsets, bitmap words,
+ * image pixels) against the extent of the buffer they address.  An index
+ * outside sets a bit in a device status word and the access is skipped;
+ * nothing traps.  The tests run the parity cases against it and expect no bit.
+ *   mctp_checked_build    1 in the checked library, 0 in the normal one
+ *   mctp_checked_status   waits for the device, ORs the status words into
+ *                         *bits (1 histogram bin, 4 atlas write, 8 atlas read,
+ *                         16 table read, 32 image pixel, 64 keep-table entry,
+ *                         2^31 self-test) and clears them when reset != 0;
+ *                         MCTP_EUNSUPPORTED in the normal library
+ *   mctp_checked_selftest enqueues one check of an index outside its extent
+ *                         (it sets the self-test bit and accesses nothing)
+ * The paper has no counterpart; this is test infrastructure of the library.
+ */
+int mctp_checked_build(void);
+int mctp_checked_status(uint32_t *bits, int32_t reset);
+int mctp_checked_selftest(void *stream);
+
 /* MCTP_ABI_VERSION of the loaded library. */
 int mctp_version(void);
 

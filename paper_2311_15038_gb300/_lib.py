@@ -94,6 +94,9 @@ EXPORTS = {
     "mctp_server_poll": ([C_VP, ctypes.POINTER(ServeResult), C_I32, ctypes.POINTER(C_I32)], ctypes.c_int),
     "mctp_server_release": ([C_VP, ctypes.c_uint64], ctypes.c_int),
     "mctp_server_cancel": ([C_VP, ctypes.c_uint64], ctypes.c_int),
+    "mctp_checked_build": ([], ctypes.c_int),
+    "mctp_checked_status": ([ctypes.POINTER(ctypes.c_uint32), C_I32], ctypes.c_int),
+    "mctp_checked_selftest": ([C_VP], ctypes.c_int),
     "mctp_server_inject_launch_failures": ([C_VP, C_I32], ctypes.c_int),
     "mctp_server_stats": ([C_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -133,14 +136,16 @@ class MctpError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process uses: libmctp.so, or with MCTP_LIBRARY=checked
+    in the environment the checked build (bounds-tested kernels)."""
+    return _build.LIB_CHECKED if os.environ.get("MCTP_LIBRARY") == "checked" else _build.LIB
 
 
 def load():
-    """Load libmctp.so.  There is no fallback: a missing library is an error."""
+    """Load the library.  There is no fallback: a missing library is an error."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"libmctp.so not built ({path}); run __graft_entry__.build()")
         lib = ctypes.CDLL(path)

@@ -11,14 +11,16 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmctp.so")
+LIB_CHECKED = os.path.join(BUILD, "checked", "libmctp_checked.so")  # kernels compiled with MCTP_CHECKED
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(ROOT, "include")]
 
 
-def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-    cmd = ["nvcc", *NVCC_FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose_ptxas: bool, checked: bool = False) -> tuple[str, str]:
+    out = os.path.join(BUILD, "checked") if checked else BUILD
+    obj = os.path.join(out, os.path.basename(src).replace(".cu", ".o"))
+    cmd = ["nvcc", *NVCC_FLAGS, *(["-DMCTP_CHECKED"] if checked else []), "-c", src, "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -27,20 +29,27 @@ def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
     return obj, r.stderr
 
 
-def build(verbose_ptxas: bool = False) -> str:
-    """Compile every csrc/*.cu and link libmctp.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose_ptxas: bool = False, checked: bool = True) -> str:
+    """Compile every csrc/*.cu and link libmctp.so (and, with checked, the
+    bounds-tested libmctp_checked.so from the same sources); returns the
+    path of libmctp.so."""
+    os.makedirs(os.path.join(BUILD, "checked"), exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    objs = [o for o, _ in results]
+    jobs = [(src, False) for src in srcs] + ([(src, True) for src in srcs] if checked else [])
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), 2 * (os.cpu_count() or 4))) as ex:
+        results = list(ex.map(lambda j: _compile(j[0], verbose_ptxas and not j[1], j[1]), jobs))
+    objs = [o for (o, _), (_, chk) in zip(results, jobs) if not chk]
     if verbose_ptxas:
         with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
-            for (_, log), src in zip(results, srcs):
-                f.write(f"== {os.path.basename(src)}\n{log}\n")
-    tmp = LIB + ".tmp"
-    subprocess.check_call(["nvcc", "-shared", *ARCH, "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+            for (_, log), (src, chk) in zip(results, jobs):
+                if not chk:
+                    f.write(f"== {os.path.basename(src)}\n{log}\n")
+    for lib, these in ((LIB, objs), (LIB_CHECKED, [o for (o, _), (_, chk) in zip(results, jobs) if chk])):
+        if not these:
+            continue
+        tmp = lib + ".tmp"
+        subprocess.check_call(["nvcc", "-shared", *ARCH, "-o", tmp, *these])
+        os.replace(tmp, lib)
     return LIB
 
 

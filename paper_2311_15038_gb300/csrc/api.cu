@@ -42,3 +42,52 @@ extern "C" size_t mctp_maxgrid_bytes(int32_t mx, int32_t my, int32_t mz)
     const size_t c = MCTP_MAXGRID_CELL;
     return ((size_t(mx) + c - 1) / c) * ((size_t(my) + c - 1) / c) * ((size_t(mz) + c - 1) / c) * sizeof(uint16_t);
 }
+
+// ---- checked build (MCTP_CHECKED): index faults recorded by the kernels
+namespace mctp {
+int fault_word_hist(uint32_t *bits, bool reset);
+int fault_word_threshold(uint32_t *bits, bool reset);
+int fault_word_slicemap(uint32_t *bits, bool reset);
+int fault_word_render(uint32_t *bits, bool reset);
+int fault_word_render_batch(uint32_t *bits, bool reset);
+MCTP_FAULT_READER(api)
+namespace {
+// Records the self-test bit through the same check the kernels use (an index
+// outside a 3-element extent); nothing is read or written.
+__global__ void checked_selftest_kernel()
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)in_range(5, 3, kFaultSelfTest);
+}
+}  // namespace
+}  // namespace mctp
+
+extern "C" int mctp_checked_build(void)
+{
+#ifdef MCTP_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" int mctp_checked_status(uint32_t *bits, int32_t reset)
+{
+    using namespace mctp;
+    if (!bits) return MCTP_EINVAL;
+    *bits = 0;
+    if (!mctp_checked_build()) return MCTP_EUNSUPPORTED;
+    int (*const readers[])(uint32_t *, bool) = {fault_word_hist, fault_word_threshold, fault_word_slicemap,
+                                                fault_word_render, fault_word_render_batch, fault_word_api};
+    for (auto f : readers) {
+        const int rc = f(bits, reset != 0);
+        if (rc != MCTP_OK) return rc;
+    }
+    return MCTP_OK;
+}
+
+extern "C" int mctp_checked_selftest(void *stream)
+{
+    if (!mctp_checked_build()) return MCTP_EUNSUPPORTED;
+    mctp::checked_selftest_kernel<<<1, 32, 0, mctp::as_stream(stream)>>>();
+    return mctp::launch_status();
+}

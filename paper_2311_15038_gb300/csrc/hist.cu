@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kHistThreads)
             ++ovf;
             return;
         }
-        atomicAdd(&mine[(v >> lane_shift) << 5], 1u);
+        if (in_range(v >> lane_shift, nbins, kFaultHistBin)) atomicAdd(&mine[(v >> lane_shift) << 5], 1u);
     };
     const int64_t tail0 = head + nvec * E;
     for (int64_t i = tid; i < head; i += nthreads) count(base[i]);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kWinThreads, 1)
         if (kCheckOverflow) bin = min(bin, nb);
         const uint32_t d = bin - lo;  // wraps for bins below the window
         uint32_t *const at = d < uint32_t(kWinBins) ? hot_lane + (d << 5) : plain + bin;
-        atomicAdd(at, 1u);
+        if (in_range(bin, nbins + 1, kFaultHistBin)) atomicAdd(at, 1u);
     };
     auto count_vec = [&](const uint4 &q) {
         const uint32_t w[4] = {q.x, q.y, q.z, q.w};
@@ -249,7 +249,7 @@ __global__ void hist_global_kernel(const T *__restrict__ base, int64_t n, int sh
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += nthreads) {
         uint32_t v = base[i];
         if (v >= limit) atomicAdd(overflow, 1ull);
-        else atomicAdd(&hist[v >> shift], 1ull);
+        else if (in_range(v >> shift, limit >> shift, kFaultHistBin)) atomicAdd(&hist[v >> shift], 1ull);
     }
 }
 
@@ -309,6 +309,9 @@ int launch_hist(const T *base, int64_t n, int bits, int nbins, uint64_t *hist, u
 }
 
 }  // namespace
+
+MCTP_FAULT_READER(hist)
+
 }  // namespace mctp
 
 extern "C" int mctp_build_histogram(const void *vol, const mctp_volume_desc *d, int64_t z0, int64_t z1,

@@ -10,6 +10,51 @@ namespace mctp {
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// ---- checked build
+// Compiled with MCTP_CHECKED (the second library the build makes for tests),
+// the kernels test their main indices against the extent of the buffer they
+// address.  An index outside records a bit in a device status word of its
+// translation unit and the access is skipped: nothing traps and nothing is
+// read or written out of range.  In the normal build the test is the constant
+// true and costs nothing.
+enum : unsigned {
+    kFaultHistBin = 1u,      // a histogram bin (shared or global counters)
+    kFaultAtlasWrite = 4u,   // a slicemap atlas element written
+    kFaultAtlasRead = 8u,    // an atlas element read by a march
+    kFaultTableRead = 16u,   // a transfer-function entry, slice offset or bitmap word
+    kFaultImageWrite = 32u,  // a pixel of an output image
+    kFaultKeepRead = 64u,    // a keep-table entry
+    kFaultSelfTest = 0x80000000u,
+};
+#ifdef MCTP_CHECKED
+static __device__ unsigned int g_fault_word;
+__device__ __forceinline__ bool in_range(long long i, long long n, unsigned bit)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_fault_word, bit);
+    return false;
+}
+// This translation unit's fault word (waits for the device), cleared on request.
+static inline int tu_fault_word(uint32_t *bits, bool reset)
+{
+    unsigned int v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(&v, g_fault_word, sizeof(v)) != cudaSuccess)
+        return MCTP_ECUDA;
+    *bits |= v;
+    if (reset) {
+        const unsigned int z = 0;
+        if (cudaMemcpyToSymbol(g_fault_word, &z, sizeof(z)) != cudaSuccess) return MCTP_ECUDA;
+    }
+    return MCTP_OK;
+}
+#define MCTP_FAULT_READER(name) \
+    int fault_word_##name(uint32_t *bits, bool reset) { return tu_fault_word(bits, reset); }
+#else
+__device__ __forceinline__ constexpr bool in_range(long long, long long, unsigned) { return true; }
+#define MCTP_FAULT_READER(name) \
+    int fault_word_##name(uint32_t *, bool) { return MCTP_OK; }
+#endif
+
 inline int log2_exact(int64_t v)
 {
     if (v <= 0 || (v & (v - 1)) != 0) return -1;

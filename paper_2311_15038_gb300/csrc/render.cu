@@ -43,6 +43,7 @@ struct RenderParams {
     int32_t vmax_int;
     int32_t pad;
     int64_t total_tiles;
+    int64_t out4_total;  // float4 pixels of the output (bounds of the checked build)
     const float4 *lut;
     float *out;
     unsigned long long *samples;
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
             G.pitch = uint32_t(Lv.pitch);
             G.wpr = (Lv.gx + 31) / 32;
             G.gy = Lv.gy;
+            G.elems = Lv.pitch * ((Lv.mz + Lv.tiles_x - 1) / Lv.tiles_x) * Lv.my;
             const int nrows = Lv.gy * Lv.gz;
             use_skip = Lv.maxgrid != nullptr && skip_S >= 0 && int64_t(nrows) * G.wpr <= kMaxBitmapWords;
             if (use_skip)
@@ -104,7 +106,8 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
         if (px >= V.W || py >= V.H) continue;
         const float4 acc = march_ray<T>(V, static_cast<const T *>(Lv.atlas), G, use_skip, tab, P.nlut,
                                         P.inv_vmax, P.alpha_stop, px, py, taken, evaluated);
-        reinterpret_cast<float4 *>(P.out + V.out_offset)[int64_t(py) * V.W + px] = acc;
+        const int64_t pix = V.out_offset / 4 + int64_t(py) * V.W + px;
+        if (in_range(pix, P.out4_total, kFaultImageWrite)) reinterpret_cast<float4 *>(P.out)[pix] = acc;
         flush_count(taken, P.samples);
         evaluated = 0;
     }
@@ -112,6 +115,9 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_kernel(const __grid_
 }
 
 }  // namespace
+
+MCTP_FAULT_READER(render)
+
 }  // namespace mctp
 
 extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views, int32_t nviews,
@@ -170,6 +176,8 @@ extern "C" int mctp_render_views(const mctp_slicemap *sm, const mctp_view *views
     per_sm = std::max(per_sm, 1);
 
     int64_t out_off = 0;
+    P.out4_total = 0;
+    for (int i = 0; i < nviews; ++i) P.out4_total += int64_t(views[i].width) * views[i].height;
     for (int first = 0; first < nviews; first += kMaxViewsPerLaunch) {
         const int cnt = std::min(kMaxViewsPerLaunch, nviews - first);
         int64_t tiles = 0;

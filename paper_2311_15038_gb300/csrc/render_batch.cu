@@ -107,6 +107,7 @@ struct BatchArgs {
     int32_t wx_log2;  // log2 warp_w
     int32_t chunk;
     float alpha_stop;
+    int64_t out4_total;  // float4 pixels the output buffer holds (bounds of the checked build)
 };
 
 __global__ void __launch_bounds__(kBatchThreads) batch_upload_kernel(const __grid_constant__ UploadArgs A)
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __
             const int py = int(sty << (gyl + wyl)) + int((sub >> gxl) << wyl) + ly;
             if (px >= BV.vp.W || py >= BV.vp.H) continue;
             const BatchPair &PR = P.pairs[BV.pair];
-            const LevelGeom G{{PR.mx - 1, PR.my - 1, PR.mz - 1}, uint32_t(PR.pitch), PR.gy, PR.wpr};
+            const LevelGeom G{{PR.mx - 1, PR.my - 1, PR.mz - 1}, uint32_t(PR.pitch), PR.gy, PR.wpr,
+                              PR.pitch * ((PR.mz + PR.tiles_x - 1) / PR.tiles_x) * PR.my};
             const float4 *lut = (kLutShared ? slut : P.luts) + int64_t(PR.lut) * P.nlut;
             DepthRange range{false, 0u, 0u};
             if (P.bounds_lo) {
@@ -303,7 +305,8 @@ __global__ void __launch_bounds__(kBatchThreads, 4) render_batch_kernel(const __
                 acc = march_ray<T, kCount>(BV.vp, static_cast<const T *>(PR.atlas), G, PR.use_skip != 0, tab, P.nlut,
                                            PR.inv_vmax, P.alpha_stop, px, py, taken, evaluated, range);
             }
-            reinterpret_cast<float4 *>(P.out + BV.vp.out_offset)[int64_t(py) * BV.vp.W + px] = acc;
+            const int64_t pix = BV.vp.out_offset / 4 + int64_t(py) * BV.vp.W + px;
+            if (in_range(pix, P.out4_total, kFaultImageWrite)) reinterpret_cast<float4 *>(P.out)[pix] = acc;
             flush_count(taken, P.samples);
             if (kCount) flush_count(evaluated, P.counter_evaluated);
         }
@@ -409,6 +412,9 @@ int make_plan(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views, con
 }
 
 }  // namespace
+
+MCTP_FAULT_READER(render_batch)
+
 }  // namespace mctp
 
 extern "C" int mctp_render_batch_workspace(const mctp_slicemap *sms, int32_t nsm, const mctp_view *views,
@@ -592,6 +598,15 @@ int render_batch_impl(const mctp_slicemap *sms, int32_t nsm, const mctp_view *vi
     P.wx_log2 = wxl;
     P.chunk = tun.chunk;
     P.alpha_stop = alpha_stop;
+    P.out4_total = 0;
+    {
+        int64_t off = 0;
+        for (int i = 0; i < nviews; ++i) {
+            const int64_t first = out_offsets ? out_offsets[i] : off;
+            P.out4_total = std::max<int64_t>(P.out4_total, first / 4 + int64_t(views[i].width) * views[i].height);
+            off += int64_t(views[i].width) * views[i].height * 4;
+        }
+    }
     const size_t lut_bytes = size_t(nluts) * size_t(nlut) * sizeof(float4);
     const bool lut_shared = lut_bytes <= kLutSmemMax;
     const size_t smem = lut_shared ? lut_bytes : 0;

@@ -60,6 +60,7 @@ struct LevelGeom {
     uint32_t pitch;  // elements per atlas row
     int32_t gy;      // bitmap: cells along y
     int32_t wpr;     // bitmap: 32-bit words per (cz, cy) row
+    int64_t elems;   // atlas elements of the level's tiles (bounds of the checked build)
 };
 
 template <typename T>
@@ -309,7 +310,9 @@ struct RayMarch {
 template <class Tab>
 __device__ __forceinline__ bool cell_marked(const Tab &tab, const LevelGeom &G, const int cc[3])
 {
-    const uint32_t word = tab.occ_at((cc[2] * G.gy + cc[1]) * G.wpr + (cc[0] >> 5));
+    const int w = (cc[2] * G.gy + cc[1]) * G.wpr + (cc[0] >> 5);
+    if (!in_range(w, int64_t((G.m1[2] >> 3) + 1) * G.gy * G.wpr, kFaultTableRead)) return true;
+    const uint32_t word = tab.occ_at(w);
     return (word >> (cc[0] & 31)) & 1u;
 }
 
@@ -412,8 +415,9 @@ __device__ __forceinline__ bool march_step(RayMarch &S, const ViewParams &V, con
     if (iz != S.zc) {
         // the slice pair changes only when the sample's lower corner leaves its slice
         S.zc = iz;
-        S.za = tab.slice_at(min(max(iz, 0), Mm1[2]));
-        S.zb = tab.slice_at(min(max(iz + 1, 0), Mm1[2]));
+        const int za = min(max(iz, 0), Mm1[2]), zb = min(max(iz + 1, 0), Mm1[2]);
+        S.za = in_range(za, Mm1[2] + 1, kFaultTableRead) ? tab.slice_at(za) : 0u;
+        S.zb = in_range(zb, Mm1[2] + 1, kFaultTableRead) ? tab.slice_at(zb) : 0u;
     }
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if constexpr (Tab::kGather) {
@@ -427,14 +431,14 @@ __device__ __forceinline__ bool march_step(RayMarch &S, const ViewParams &V, con
         const int x1 = min(max(ix + 1, 0), Mm1[0]), y1i = min(max(iy + 1, 0), Mm1[1]);
         const uint32_t pitch = G.pitch;
         const uint32_t ya = uint32_t(y0i) * pitch, yb = uint32_t(y1i) * pitch;
-        v000 = texel(atlas, S.za + ya + x0);
-        v100 = texel(atlas, S.za + ya + x1);
-        v010 = texel(atlas, S.za + yb + x0);
-        v110 = texel(atlas, S.za + yb + x1);
-        v001 = texel(atlas, S.zb + ya + x0);
-        v101 = texel(atlas, S.zb + ya + x1);
-        v011 = texel(atlas, S.zb + yb + x0);
-        v111 = texel(atlas, S.zb + yb + x1);
+        v000 = in_range(int64_t(S.za + ya + x0), G.elems, kFaultAtlasRead) ? texel(atlas, S.za + ya + x0) : 0.f;
+        v100 = in_range(int64_t(S.za + ya + x1), G.elems, kFaultAtlasRead) ? texel(atlas, S.za + ya + x1) : 0.f;
+        v010 = in_range(int64_t(S.za + yb + x0), G.elems, kFaultAtlasRead) ? texel(atlas, S.za + yb + x0) : 0.f;
+        v110 = in_range(int64_t(S.za + yb + x1), G.elems, kFaultAtlasRead) ? texel(atlas, S.za + yb + x1) : 0.f;
+        v001 = in_range(int64_t(S.zb + ya + x0), G.elems, kFaultAtlasRead) ? texel(atlas, S.zb + ya + x0) : 0.f;
+        v101 = in_range(int64_t(S.zb + ya + x1), G.elems, kFaultAtlasRead) ? texel(atlas, S.zb + ya + x1) : 0.f;
+        v011 = in_range(int64_t(S.zb + yb + x0), G.elems, kFaultAtlasRead) ? texel(atlas, S.zb + yb + x0) : 0.f;
+        v111 = in_range(int64_t(S.zb + yb + x1), G.elems, kFaultAtlasRead) ? texel(atlas, S.zb + yb + x1) : 0.f;
     }
     const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
     const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
@@ -442,7 +446,9 @@ __device__ __forceinline__ bool march_step(RayMarch &S, const ViewParams &V, con
     const float x = lut_coord(fmaf(fz, c1 - c0, c0), inv_vmax, float(nlut - 1));
     const int j = min(int(x), nlut - 2);
     const float fl = x - float(j);
-    const float4 e0 = tab.lut_at(j), e1 = tab.lut_at(j + 1);
+    const bool lut_ok = in_range(j, nlut - 1, kFaultTableRead);
+    const float4 e0 = lut_ok ? tab.lut_at(j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 e1 = lut_ok ? tab.lut_at(j + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float ca = fmaf(fl, e1.w - e0.w, e0.w);
     const float w = (1.0f - S.A) * ca;
     S.C0 = fmaf(w, fmaf(fl, e1.x - e0.x, e0.x), S.C0);

@@ -54,6 +54,7 @@ struct L0Args {
     T *atlas[kMaxFused + 1];
     int32_t tiles_x[kMaxFused + 1];
     int64_t pitch[kMaxFused + 1];  // atlas row pitch in elements
+    int64_t elems[kMaxFused + 1];  // atlas elements (bounds of the checked build)
     const uint8_t *keep;        // nullptr: no filtering
     int32_t nbins;
     int32_t shift;
@@ -256,7 +257,7 @@ __device__ void level0_group(const L0Args<T> &a, int Z0, int Y0, int gz, int gy,
                 for (uint32_t k = 0; k < xw; ++k) sum += cs[k];
                 const uint32_t cnt = xw * R;
                 const uint32_t val = (sum + cnt / 2u) / cnt;
-                a.atlas[0][row_off[b][jj] + x] = (T)val;
+                if (in_range(row_off[b][jj] + x, a.elems[0], kFaultAtlasWrite)) a.atlas[0][row_off[b][jj] + x] = (T)val;
                 if (grp) grp[(g0 + jj) * a.mx + x] = uint16_t(val);
             }
         }
@@ -315,7 +316,8 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
                     s += uint32_t(src[0]) + uint32_t(src[1]);
                 }
             const uint32_t val = (s + 4u) / 8u;
-            *atlas_ptr(a.atlas[1], a.pitch[1], a.tiles_x[1], hx, my1, x, Y0 / 2 + b, Z0 / 2 + c) = (T)val;
+            T *w1 = atlas_ptr(a.atlas[1], a.pitch[1], a.tiles_x[1], hx, my1, x, Y0 / 2 + b, Z0 / 2 + c);
+            if (in_range(w1 - a.atlas[1], a.elems[1], kFaultAtlasWrite)) *w1 = (T)val;
             if (a.fused > 1) grp1[(c * hy + b) * hx + x] = uint16_t(val);
         }
     }
@@ -335,8 +337,8 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
                     const uint16_t *src = grp1 + ((2 * c + dz) * gy1 + (2 * b + dy)) * mx1 + 2 * x;
                     s += uint32_t(src[0]) + uint32_t(src[1]);
                 }
-            *atlas_ptr(a.atlas[2], a.pitch[2], a.tiles_x[2], hx, my2, x, Y0 / 4 + b, Z0 / 4 + c) =
-                (T)((s + 4u) / 8u);
+            T *w2 = atlas_ptr(a.atlas[2], a.pitch[2], a.tiles_x[2], hx, my2, x, Y0 / 4 + b, Z0 / 4 + c);
+            if (in_range(w2 - a.atlas[2], a.elems[2], kFaultAtlasWrite)) *w2 = (T)((s + 4u) / 8u);
         }
     }
 }
@@ -364,6 +366,7 @@ struct RowsArgs {
     uint8_t *atlas;
     int32_t tiles_x;
     int64_t pitch;
+    int64_t elems;  // atlas elements (bounds of the checked build)
     const uint8_t *keep;
     int32_t nbins, shift;
     uint32_t limit;
@@ -522,7 +525,8 @@ __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(co
             uint32_t sum = 0;
             for (int c = c0; c < c1; ++c) sum += mine[c + (c >> 5) * 8];
             const uint32_t cnt = uint32_t(c1 - c0) * uint32_t(R);
-            out[x] = uint8_t(div_round(sum, cnt, 1.0f / float(cnt)));
+            if (in_range((out - a.atlas) + x, a.elems, kFaultAtlasWrite))
+                out[x] = uint8_t(div_round(sum, cnt, 1.0f / float(cnt)));
         }
         __syncwarp();
     }
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(co
 template <typename T>
 __global__ void __launch_bounds__(256) halve_kernel(const T *__restrict__ src, int64_t src_pitch, int src_tx, int mx,
                                                      int my, T *__restrict__ dst, int64_t dst_pitch, int dst_tx,
-                                                     int64_t total)
+                                                     int64_t total, int64_t dst_elems)
 {
     const int hx = mx / 2, hy = my / 2;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
@@ -547,7 +551,8 @@ __global__ void __launch_bounds__(256) halve_kernel(const T *__restrict__ src, i
                 const T *p = atlas_ptr(const_cast<T *>(src), src_pitch, src_tx, mx, my, 2 * x, 2 * y + dy, 2 * z + dz);
                 s += uint32_t(__ldg(p)) + uint32_t(__ldg(p + 1));
             }
-        *atlas_ptr(dst, dst_pitch, dst_tx, hx, hy, x, y, z) = (T)((s + 4u) / 8u);
+        T *w = atlas_ptr(dst, dst_pitch, dst_tx, hx, hy, x, y, z);
+        if (in_range(w - dst, dst_elems, kFaultAtlasWrite)) *w = (T)((s + 4u) / 8u);
     }
 }
 
@@ -639,6 +644,7 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
         a.atlas = static_cast<uint8_t *>(sm->atlas[0]);
         a.tiles_x = sm->tiles_x[0];
         a.pitch = int64_t(sm->tiles_x[0]) * sm->dims[0][0];
+        a.elems = a.pitch * sm->tiles_y[0] * sm->dims[0][1];
         a.keep = keep;
         a.nbins = keep ? nbins : 0;
         a.shift = keep ? bin_shift(d->bits, nbins) : 0;
@@ -671,6 +677,7 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
             a.atlas[k] = static_cast<T *>(sm->atlas[k]);
             a.tiles_x[k] = sm->tiles_x[k];
             a.pitch[k] = int64_t(sm->tiles_x[k]) * sm->dims[k][0];
+            a.elems[k] = a.pitch[k] * sm->tiles_y[k] * sm->dims[k][1];
         }
         a.keep = keep;
         a.nbins = keep ? nbins : 0;
@@ -711,7 +718,8 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
         const int64_t grid = std::min<int64_t>((total + 255) / 256, int64_t(num_sms()) * 16);
         halve_kernel<T><<<unsigned(std::max<int64_t>(grid, 1)), 256, 0, s>>>(
             static_cast<const T *>(sm->atlas[k - 1]), int64_t(sm->tiles_x[k - 1]) * mx, sm->tiles_x[k - 1], mx, my,
-            static_cast<T *>(sm->atlas[k]), int64_t(sm->tiles_x[k]) * sm->dims[k][0], sm->tiles_x[k], total);
+            static_cast<T *>(sm->atlas[k]), int64_t(sm->tiles_x[k]) * sm->dims[k][0], sm->tiles_x[k], total,
+            int64_t(sm->tiles_x[k]) * sm->dims[k][0] * sm->tiles_y[k] * sm->dims[k][1]);
         rc = launch_status();
         if (rc != MCTP_OK) return rc;
     }
@@ -753,6 +761,8 @@ int check_slicemap(const mctp_slicemap *sm)
     }
     return MCTP_OK;
 }
+
+MCTP_FAULT_READER(slicemap)
 
 }  // namespace mctp
 

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kSelThreads)
 template <typename T>
 __device__ __forceinline__ uint32_t keep_value(uint32_t v, const uint8_t *lut, int shift, uint32_t limit)
 {
-    return (v < limit && lut[v >> shift]) ? v : 0u;
+    return (v < limit && in_range(v >> shift, limit >> shift, kFaultKeepRead) && lut[v >> shift]) ? v : 0u;
 }
 
 template <typename T>
@@ -284,6 +284,9 @@ int launch_filter(const T *in, T *out, int64_t n, const uint8_t *keep, int nbins
 }
 
 }  // namespace
+
+MCTP_FAULT_READER(threshold)
+
 }  // namespace mctp
 
 extern "C" int mctp_select_threshold(const uint64_t *hist, int32_t nbins, const mctp_thr_params *p,

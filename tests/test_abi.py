@@ -360,3 +360,11 @@ def test_binding_refuses_short_or_mistyped_outputs():
         mctp._out(torch.empty(1, dtype=torch.int64), "samples", torch.uint64, 1, None)
     with pytest.raises(ValueError, match="CUDA"):
         mctp._out(torch.empty(64, dtype=torch.float32), "out", torch.float32, 16, None)
+
+
+def test_normal_library_is_not_the_checked_build(lib):
+    import ctypes
+    assert lib.mctp_checked_build() == 0
+    bits = ctypes.c_uint32(7)
+    assert lib.mctp_checked_status(ctypes.byref(bits), 0) == -2 and bits.value == 0
+    assert lib.mctp_checked_selftest(None) == -2
