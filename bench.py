@@ -251,6 +251,16 @@ def launches_per_step(wl, nviews, ntex):
     return (1 + 1 + 1 + max(0, nl - 3) + nl + ntex + 3 + (nviews + 127) // 128 + (nviews + 1023) // 1024 + 2)
 
 
+def batch_launches_per_step(nvol, nviews):
+    """Kernels of this library launched by one pass of the batched workload:
+    the histograms, the keep tables, the max grids and the texture updates of
+    up to 64 volumes per launch, one level-0 kernel per volume, and the
+    work-queue renderer (set-up, depth bounds, one view upload per 128 views,
+    render)."""
+    per64 = (nvol + 63) // 64
+    return 3 * per64 + 1 + nvol + 3 + (nviews + 127) // 128
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -926,7 +936,7 @@ def run_batch(args, wl):
         autotune_ms={f"w{t.warp_w}c{t.chunk}k{t.ctas_per_sm}": ms for t, ms in tune_ms.items()},
         latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
         roofline=roof,
-        gpu_launches=(4 * len(items) + 1 + (n_views + 127) // 128 + 1) * args.steps,
+        gpu_launches=batch_launches_per_step(len(items), n_views) * args.steps,
         clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")),
         e2e=dict(value=samples_per_step / e2e_s, unit=UNIT, h2d_bytes_per_step=vol_bytes,
                  d2h_bytes_per_step=pipe.images.numel() * 4, ms_per_step=e2e_s * 1e3),

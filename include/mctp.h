@@ -135,6 +135,12 @@ typedef struct {
 typedef struct mctp_atlas_texture mctp_atlas_texture;
 int mctp_atlas_texture_create(const mctp_slicemap *sm, int32_t level, mctp_atlas_texture **out, uint64_t *handle);
 int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slicemap *sm, int32_t level, void *stream);
+/* mctp_atlas_texture_update for `count` textures in one launch: textures[i]
+ * receives level levels[i] of sms[i] (host arrays of count entries; every
+ * slicemap of one dtype).  Errors as mctp_atlas_texture_update, MCTP_EINVAL
+ * also for count < 0 or mixed dtypes; count == 0 launches nothing. */
+int mctp_atlas_texture_update_batch(mctp_atlas_texture *const *textures, const mctp_slicemap *sms,
+                                    const int32_t *levels, int32_t count, void *stream);
 int mctp_atlas_texture_destroy(mctp_atlas_texture *t);
 
 /* One orthographic view of a slicemap level.  The camera looks at the centre
@@ -165,6 +171,20 @@ int mctp_build_histogram(const void *vol, const mctp_volume_desc *d, int64_t z0,
                          int32_t nbins, uint64_t *hist, uint64_t *overflow, void *stream);
 
 /*
+ * Histograms of `count` whole volumes in one launch (the batched form of
+ * mctp_build_histogram over z in [0, nz)): vols[i] described by descs[i]
+ * (host arrays of count entries, every volume with the same dtype and bits)
+ * counts into hist[i nbins .. (i + 1) nbins) and overflow[i] (device uint64
+ * arrays, overwritten).  With at most 256 bins the volumes share one
+ * launch, which splits their concatenated 16-byte vectors evenly over the
+ * blocks; with more bins each volume takes its own launch.
+ * Errors: as mctp_build_histogram; MCTP_EINVAL also for count < 0 or mixed
+ *         dtype/bits.
+ */
+int mctp_build_histogram_batch(const void *const *vols, const mctp_volume_desc *descs, int32_t count,
+                               int32_t nbins, uint64_t *hist, uint64_t *overflow, void *stream);
+
+/*
  * Threshold selection -> keep table (Sec. III-A, Alg. 1 and Alg. 2;
  * Sec. III-D histogram filtering).  Computed on the device in FP64 with a
  * fixed evaluation order:
@@ -185,6 +205,20 @@ int mctp_build_histogram(const void *vol, const mctp_volume_desc *d, int64_t z0,
  */
 int mctp_select_threshold(const uint64_t *hist, int32_t nbins, const mctp_thr_params *p,
                           uint8_t *keep_lut, int32_t *result, void *stream);
+
+/*
+ * Threshold selection for `count` histograms in one launch (one block per
+ * histogram; the batched form of mctp_select_threshold, for many volumes
+ * previewed together).  Histogram i is hist[i nbins .. (i + 1) nbins), its
+ * keep table keep_lut[i nbins ..] and its result result[4 i .. 4 i + 3]; each
+ * is computed exactly as mctp_select_threshold computes it, with the same
+ * params for every histogram.
+ *   count     number of histograms, >= 0 (0: nothing is launched)
+ * Errors: as mctp_select_threshold; MCTP_EINVAL also for count < 0 or
+ *         count > 2^31 / nbins.
+ */
+int mctp_select_threshold_batch(const uint64_t *hist, int32_t count, int32_t nbins, const mctp_thr_params *p,
+                                uint8_t *keep_lut, int32_t *result, void *stream);
 
 /*
  * Binary classification of every voxel (Sec. III-A; bins disposed of by the
@@ -218,6 +252,20 @@ int mctp_filter_threshold(const void *in, const mctp_volume_desc *d, const uint8
  */
 int mctp_build_slicemap(const void *vol, const mctp_volume_desc *d, const uint8_t *keep_lut,
                         int32_t nbins, const mctp_slicemap *sm, void *stream);
+
+/*
+ * mctp_build_slicemap for `count` volumes (many volumes previewed together):
+ * vols[i], descs[i] and sms[i] (host arrays of count entries) as in
+ * mctp_build_slicemap, keep table keep_luts[i nbins .. (i + 1) nbins) (device
+ * uint8[count][nbins], or NULL for no filtering).  Every volume has the same
+ * dtype.  The atlases are built volume by volume; the max grids of all
+ * volumes' levels are filled in one launch afterwards.  Results equal those
+ * of mctp_build_slicemap on each volume.
+ * Errors: as mctp_build_slicemap for any volume (nothing is launched then);
+ *         MCTP_EINVAL also for count < 0 or mixed dtypes.
+ */
+int mctp_build_slicemap_batch(const void *const *vols, const mctp_volume_desc *descs, const uint8_t *keep_luts,
+                              int32_t nbins, const mctp_slicemap *sms, int32_t count, void *stream);
 
 /*
  * Server-side rendering of slicemap views (Sec. III-C): orthographic

@@ -18,7 +18,9 @@ import torch
 from . import _lib
 from ._lib import MctpError  # noqa: F401
 
-__all__ = ["build_histogram", "select_threshold", "filter_threshold", "build_slicemap", "render_views",
+__all__ = ["build_histogram", "build_histogram_batch", "build_slicemap_batch", "update_textures_batch",
+           "select_threshold", "select_threshold_batch", "filter_threshold", "build_slicemap",
+           "render_views",
            "render_batch", "render_batch_workspace", "render_batch_static", "batch_samples_evaluated", "BatchTuning",
            "image_entropy",
            "find_container", "mask_container", "Slicemap", "AtlasTexture", "View", "default_tiles",
@@ -99,6 +101,34 @@ def build_histogram(vol: torch.Tensor, bits: int, nbins: int, z0: int = 0, z1: i
     return hist, overflow
 
 
+def _volume_arrays(vols, bits):
+    for v in vols:
+        _cuda(v, "vol")
+    n = len(vols)
+    return (ctypes.c_void_p * max(n, 1))(*[v.data_ptr() for v in vols]), \
+        (_lib.VolumeDesc * max(n, 1))(*[volume_desc(v, bits) for v in vols])
+
+
+def build_histogram_batch(vols: list[torch.Tensor], bits: int, nbins: int, hist: torch.Tensor | None = None,
+                          overflow: torch.Tensor | None = None, stream=None):
+    """Whole-volume histograms of every volume in vols (one dtype) in one
+    launch -> (hist uint64[count, nbins], overflow uint64[count, 1])."""
+    if not vols:
+        raise ValueError("no volumes")
+    dev = vols[0].device
+    ptrs, descs = _volume_arrays(vols, bits)
+    n = len(vols)
+    if hist is None:
+        hist = torch.empty((n, nbins), dtype=torch.uint64, device=dev)
+    if overflow is None:
+        overflow = torch.empty((n, 1), dtype=torch.uint64, device=dev)
+    _out(hist, "hist", torch.uint64, n * nbins, dev)
+    _out(overflow, "overflow", torch.uint64, n, dev)
+    _lib.check(_lib.load().mctp_build_histogram_batch(ptrs, descs, n, nbins, _ptr(hist), _ptr(overflow),
+                                                      _stream(stream)), "mctp_build_histogram_batch")
+    return hist, overflow
+
+
 def select_threshold(hist: torch.Tensor | None, nbins: int | None = None, mode: str = "otsu",
                      explicit_T: int = 0, its_max_iter: int = 256, topslab_kmin: int = 1,
                      keep: torch.Tensor | None = None, result: torch.Tensor | None = None,
@@ -119,6 +149,27 @@ def select_threshold(hist: torch.Tensor | None, nbins: int | None = None, mode: 
     _out(result, "result", torch.int32, 4, device)
     _lib.check(_lib.load().mctp_select_threshold(_ptr(hist), nbins, ctypes.byref(p), _ptr(keep), _ptr(result),
                                                  _stream(stream)), "mctp_select_threshold")
+    return keep, result
+
+
+def select_threshold_batch(hist: torch.Tensor, mode: str = "otsu", explicit_T: int = 0, its_max_iter: int = 256,
+                           topslab_kmin: int = 1, keep: torch.Tensor | None = None,
+                           result: torch.Tensor | None = None, stream=None):
+    """Keep tables of the rows of hist [count, nbins] in one launch ->
+    (keep uint8[count, nbins], result int32[count, 4]); row i as select_threshold(hist[i])."""
+    _cuda(hist, "hist")
+    if hist.dim() != 2 or hist.dtype != torch.uint64:
+        raise ValueError("hist must be uint64 [count, nbins]")
+    count, nbins = hist.shape
+    p = _lib.ThrParams(_MODES[mode], explicit_T, its_max_iter, 0, topslab_kmin)
+    if keep is None:
+        keep = torch.empty((count, nbins), dtype=torch.uint8, device=hist.device)
+    if result is None:
+        result = torch.empty((count, 4), dtype=torch.int32, device=hist.device)
+    _out(keep, "keep", torch.uint8, count * nbins, hist.device)
+    _out(result, "result", torch.int32, count * 4, hist.device)
+    _lib.check(_lib.load().mctp_select_threshold_batch(_ptr(hist), count, nbins, ctypes.byref(p), _ptr(keep),
+                                                       _ptr(result), _stream(stream)), "mctp_select_threshold_batch")
     return keep, result
 
 
@@ -257,6 +308,42 @@ def build_slicemap(vol: torch.Tensor, bits: int, sm: Slicemap, keep: torch.Tenso
     _lib.check(_lib.load().mctp_build_slicemap(_ptr(vol), ctypes.byref(d), _ptr(keep), nb, ctypes.byref(s),
                                                _stream(stream)), "mctp_build_slicemap")
     return sm
+
+
+def build_slicemap_batch(vols: list[torch.Tensor], bits: int, sms: list[Slicemap],
+                         keep: torch.Tensor | None = None, stream=None) -> list[Slicemap]:
+    """build_slicemap for every (vols[i], sms[i]) with keep table keep[i]
+    (uint8 [count, nbins], or None); the max grids of all of them are filled
+    in one launch."""
+    if len(vols) != len(sms):
+        raise ValueError("one slicemap per volume")
+    if not vols:
+        return sms
+    ptrs, descs = _volume_arrays(vols, bits)
+    n = len(vols)
+    smd = (_lib.SlicemapDesc * n)(*[sm.desc() for sm in sms])
+    nb = 0
+    if keep is not None:
+        _cuda(keep, "keep")
+        if keep.dim() != 2 or keep.shape[0] < n or keep.dtype != torch.uint8:
+            raise ValueError("keep must be uint8 [count, nbins]")
+        nb = keep.shape[1]
+    _lib.check(_lib.load().mctp_build_slicemap_batch(ptrs, descs, _ptr(keep), nb, smd, n, _stream(stream)),
+               "mctp_build_slicemap_batch")
+    return sms
+
+
+def update_textures_batch(sms: list[Slicemap], stream=None) -> None:
+    """Slicemap.update_textures for every slicemap in one launch."""
+    items = [(t, sm) for sm in sms for t in (sm.textures or []) if t is not None]
+    if not items:
+        return
+    n = len(items)
+    tex = (ctypes.c_void_p * n)(*[t._ptr.value for t, _ in items])
+    smd = (_lib.SlicemapDesc * n)(*[sm.desc() for _, sm in items])
+    levels = (_lib.C_I32 * n)(*[t.level for t, _ in items])
+    _lib.check(_lib.load().mctp_atlas_texture_update_batch(tex, smd, levels, n, _stream(stream)),
+               "mctp_atlas_texture_update_batch")
 
 
 @dataclass(frozen=True)

@@ -73,7 +73,12 @@ class ServeResult(ctypes.Structure):
 EXPORTS = {
     "mctp_build_histogram": ([C_VP, ctypes.POINTER(VolumeDesc), C_I64, C_I64, C_I32, C_VP, C_VP, C_VP],
                              ctypes.c_int),
+    "mctp_build_histogram_batch": ([C_VP, C_VP, C_I32, C_I32, C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_build_slicemap_batch": ([C_VP, C_VP, C_VP, C_I32, C_VP, C_I32, C_VP], ctypes.c_int),
+    "mctp_atlas_texture_update_batch": ([C_VP, C_VP, C_VP, C_I32, C_VP], ctypes.c_int),
     "mctp_select_threshold": ([C_VP, C_I32, ctypes.POINTER(ThrParams), C_VP, C_VP, C_VP], ctypes.c_int),
+    "mctp_select_threshold_batch": ([C_VP, C_I32, C_I32, ctypes.POINTER(ThrParams), C_VP, C_VP, C_VP],
+                                    ctypes.c_int),
     "mctp_filter_threshold": ([C_VP, ctypes.POINTER(VolumeDesc), C_VP, C_I32, C_VP, C_VP], ctypes.c_int),
     "mctp_build_slicemap": ([C_VP, ctypes.POINTER(VolumeDesc), C_VP, C_I32, ctypes.POINTER(SlicemapDesc), C_VP],
                             ctypes.c_int),

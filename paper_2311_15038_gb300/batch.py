@@ -13,8 +13,9 @@ from dataclasses import asdict, dataclass
 
 import torch
 
-from . import (BatchTuning, Slicemap, View, _lib, build_histogram, build_slicemap, render_batch,
-               render_batch_workspace, select_threshold)
+from . import (BatchTuning, Slicemap, View, _lib, build_histogram, build_histogram_batch, build_slicemap,
+               build_slicemap_batch, render_batch, render_batch_workspace, select_threshold, select_threshold_batch,
+               update_textures_batch)
 from ._lib import MctpError
 
 WARP_WIDTHS = (4, 8, 16, 32)
@@ -147,17 +148,33 @@ class BatchPipeline:
         self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.graph = None
 
-    def prepare(self, i: int):
-        """Histogram, keep table and slicemap of volume i (enqueued)."""
-        it, s = self.items[i], self.stream
+    def prepare(self):
+        """Histograms, keep tables and slicemaps of every volume (enqueued):
+        one histogram launch, one keep-table launch, the slicemap builds with
+        one max-grid launch, one texture launch (volumes of one dtype and bit
+        depth; otherwise volume by volume)."""
+        s = self.stream
+        vols = [it.volume for it in self.items]
+        uniform = len({(v.dtype, it.bits) for v, it in zip(vols, self.items)}) == 1
+        if not uniform:
+            for i, it in enumerate(self.items):
+                keep = None
+                if self.mode != "none":
+                    build_histogram(it.volume, it.bits, self.nbins, 0, None, self.hist[i], self.overflow[i], s)
+                    select_threshold(self.hist[i], self.nbins, self.mode, keep=self.keep[i], result=self.result[i],
+                                     stream=s)
+                    keep = self.keep[i]
+                build_slicemap(it.volume, it.bits, self.slicemaps[i], keep, s)
+                self.slicemaps[i].update_textures(s)
+            return
+        bits = self.items[0].bits
         keep = None
         if self.mode != "none":
-            build_histogram(it.volume, it.bits, self.nbins, 0, None, self.hist[i], self.overflow[i], s)
-            select_threshold(self.hist[i], self.nbins, self.mode, keep=self.keep[i], result=self.result[i],
-                             stream=s)
-            keep = self.keep[i]
-        build_slicemap(it.volume, it.bits, self.slicemaps[i], keep, s)
-        self.slicemaps[i].update_textures(s)
+            build_histogram_batch(vols, bits, self.nbins, self.hist, self.overflow, s)
+            select_threshold_batch(self.hist, self.mode, keep=self.keep, result=self.result, stream=s)
+            keep = self.keep
+        build_slicemap_batch(vols, bits, self.slicemaps, keep, s)
+        update_textures_batch(self.slicemaps, s)
 
     def render(self):
         render_batch(self.slicemaps, self.views, self.view_slicemap, self.view_lut, self.luts, self.alpha_stop,
@@ -166,8 +183,7 @@ class BatchPipeline:
     def run(self, timer=None):
         mark = timer or (lambda name: None)
         mark("prepare")
-        for i in range(len(self.items)):
-            self.prepare(i)
+        self.prepare()
         mark("render")
         self.render()
         mark("end")
@@ -176,8 +192,7 @@ class BatchPipeline:
     def autotune(self, reps: int = 2, cache_path: str | None = None):
         """Run the slicemap builds once, then tune the render launch shape on them."""
         with torch.cuda.stream(self.stream):
-            for i in range(len(self.items)):
-                self.prepare(i)
+            self.prepare()
         self.tuning, timings = autotune_render(self.slicemaps, self.views, self.view_slicemap, self.view_lut,
                                                self.luts, self.alpha_stop, self.stream, reps, self.images,
                                                self.samples, self.workspace, cache_path)

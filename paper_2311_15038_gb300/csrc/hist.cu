@@ -25,7 +25,9 @@ constexpr int kHistUnroll = 4;
 // with the lane fastest, so the 32 atomics of a warp instruction always fall
 // in 32 different banks (peaked histograms, where many lanes share a bin,
 // otherwise serialise).  The warps of a block share the table.
-template <typename T, bool kCheckOverflow>
+// kFull8: u8 data in 256 bins (bin = value), each byte taken with one byte
+// permute.
+template <typename T, bool kCheckOverflow, bool kFull8 = false>
 __global__ void __launch_bounds__(kHistThreads)
     hist_lane_kernel(const T *__restrict__ base, int64_t n, int64_t head, int64_t nvec, int shift, uint32_t limit,
                      int nbins, unsigned long long *__restrict__ hist, unsigned long long *__restrict__ overflow)
@@ -60,7 +62,13 @@ __global__ void __launch_bounds__(kHistThreads)
             const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (sizeof(T) == 1) {
+                if (sizeof(T) == 1 && kFull8) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t v = __byte_perm(w[k], 0u, 0x4440u + b);
+                        if (in_range(v, nbins, kFaultHistBin)) atomicAdd(&mine[v << 5], 1u);
+                    }
+                } else if (sizeof(T) == 1) {
 #pragma unroll
                     for (int b = 0; b < 4; ++b) count((w[k] >> (8 * b)) & 0xffu);
                 } else {
@@ -94,6 +102,110 @@ __global__ void __launch_bounds__(kHistThreads)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
         if ((threadIdx.x & 31) == 0 && ovf) atomicAdd(overflow, (unsigned long long)ovf);
+    }
+}
+
+// Histograms of up to kHistBatch whole volumes (at most 256 bins, one dtype)
+// in one launch: the volumes' 16-byte vectors, concatenated, are split evenly
+// over the blocks; a block counts its share with the per-(bin, lane) counters
+// above and adds them into a volume's histogram whenever its share moves on
+// to the next volume.  Elements before a volume's first 16-byte boundary or
+// after its last whole vector go straight to the global histogram.
+constexpr int kHistBatch = 64;
+struct HistBatch {
+    int32_t count, nbins, shift;
+    uint32_t limit;
+    unsigned long long *hist;      // [count][nbins]
+    unsigned long long *overflow;  // [count]
+    int64_t first[kHistBatch + 1]; // vector index of volume i's first vector in the concatenation
+    const void *vol[kHistBatch];
+    int64_t n[kHistBatch];         // elements
+    int32_t head[kHistBatch];      // elements before the first 16-byte boundary
+};
+
+template <typename T, bool kCheckOverflow, bool kFull8>
+__global__ void __launch_bounds__(kHistThreads) hist_lane_batch_kernel(const __grid_constant__ HistBatch b)
+{
+    extern __shared__ uint32_t sh_cols[];  // nbins * 32
+    for (int i = threadIdx.x; i < b.nbins * 32; i += blockDim.x) sh_cols[i] = 0u;
+    constexpr int E = 16 / sizeof(T);
+    // scalar head and tail elements of volumes blockIdx.x, blockIdx.x + gridDim.x, ...
+    for (int u = blockIdx.x; u < b.count; u += gridDim.x) {
+        const T *base = static_cast<const T *>(b.vol[u]);
+        const int64_t tail0 = b.head[u] + (b.first[u + 1] - b.first[u]) * E;
+        const int64_t nscal = b.head[u] + (b.n[u] - tail0);
+        for (int64_t k = threadIdx.x; k < nscal; k += blockDim.x) {
+            const uint32_t v = base[k < b.head[u] ? k : tail0 + (k - b.head[u])];
+            if (kCheckOverflow && v >= b.limit) atomicAdd(&b.overflow[u], 1ull);
+            else if (in_range(v >> b.shift, b.nbins, kFaultHistBin))
+                atomicAdd(&b.hist[int64_t(u) * b.nbins + (v >> b.shift)], 1ull);
+        }
+    }
+    __syncthreads();
+    uint32_t *mine = sh_cols + (threadIdx.x & 31);
+    uint32_t ovf = 0;
+    auto count = [&](uint32_t v) {
+        if (kCheckOverflow && v >= b.limit) {
+            ++ovf;
+            return;
+        }
+        if (in_range(v >> b.shift, b.nbins, kFaultHistBin)) atomicAdd(&mine[(v >> b.shift) << 5], 1u);
+    };
+    auto count_vector = [&](const uint4 &q) {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sizeof(T) == 1 && kFull8) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t v = __byte_perm(w[k], 0u, 0x4440u + j);
+                    if (in_range(v, 256, kFaultHistBin)) atomicAdd(&mine[v << 5], 1u);
+                }
+            } else if (sizeof(T) == 1) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) count((w[k] >> (8 * j)) & 0xffu);
+            } else {
+                count(w[k] & 0xffffu);
+                count(w[k] >> 16);
+            }
+        }
+    };
+    const int64_t total = b.first[b.count];
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = min(total, int64_t(blockIdx.x) * per), hi = min(total, lo + per);
+    int v = 0;
+    while (v < b.count - 1 && b.first[v + 1] <= lo) ++v;
+    for (int64_t pos = lo; pos < hi; ++v) {
+        const int64_t vend = min(hi, b.first[v + 1]);
+        const uint4 *body = reinterpret_cast<const uint4 *>(static_cast<const T *>(b.vol[v]) + b.head[v]);
+        const int64_t e = vend - b.first[v];
+        int64_t i = pos - b.first[v] + threadIdx.x;
+        for (; i + (kHistUnroll - 1) * int64_t(blockDim.x) < e; i += kHistUnroll * int64_t(blockDim.x)) {
+            uint4 q[kHistUnroll];
+#pragma unroll
+            for (int u = 0; u < kHistUnroll; ++u) q[u] = ld_stream_v4(body + i + u * int64_t(blockDim.x));
+#pragma unroll
+            for (int u = 0; u < kHistUnroll; ++u) count_vector(q[u]);
+        }
+        for (; i < e; i += blockDim.x) count_vector(ld_stream_v4(body + i));
+        __syncthreads();
+        for (int bin = threadIdx.x; bin < b.nbins; bin += blockDim.x) {
+            unsigned long long sum = 0;
+            for (int l = 0; l < 32; ++l) {
+                const int w = bin * 32 + ((l + bin) & 31);  // rotated: no bank conflicts
+                sum += sh_cols[w];
+                sh_cols[w] = 0u;
+            }
+            if (sum) atomicAdd(&b.hist[int64_t(v) * b.nbins + bin], sum);
+        }
+        if (kCheckOverflow) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
+            if ((threadIdx.x & 31) == 0 && ovf) atomicAdd(&b.overflow[v], (unsigned long long)ovf);
+            ovf = 0;
+        }
+        __syncthreads();
+        pos = vend;
     }
 }
 
@@ -273,7 +385,9 @@ int launch_hist(const T *base, int64_t n, int bits, int nbins, uint64_t *hist, u
         int64_t head = int64_t(((16 - (addr0 & 15)) & 15) / sizeof(T));
         if (head > n) head = n;
         const int64_t nvec = (n - head) / (16 / int64_t(sizeof(T)));
-        auto kern = check ? hist_lane_kernel<T, true> : hist_lane_kernel<T, false>;
+        auto kern = check ? hist_lane_kernel<T, true>
+                          : (sizeof(T) == 1 && nbins == 256 ? hist_lane_kernel<T, false, true>
+                                                            : hist_lane_kernel<T, false>);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHistThreads, smem);
         per_sm = std::max(per_sm, 1);
@@ -308,6 +422,56 @@ int launch_hist(const T *base, int64_t n, int bits, int nbins, uint64_t *hist, u
     return MCTP_EINVAL;  // not reached: nbins > 16384 takes the global kernel above
 }
 
+// Whole-volume histograms of vols[0..count) (one dtype, at most 256 bins),
+// kHistBatch volumes per launch.
+template <typename T>
+int launch_hist_batch(const void *const *vols, const mctp_volume_desc *descs, int count, int nbins,
+                      uint64_t *hist, uint64_t *overflow, cudaStream_t s)
+{
+    const int bits = descs[0].bits;
+    const int shift = bin_shift(bits, nbins);
+    const bool check = !(sizeof(T) == 1 && bits == 8) && !(sizeof(T) == 2 && bits == 16);
+    auto kern = check ? hist_lane_batch_kernel<T, true, false>
+                      : (sizeof(T) == 1 && nbins == 256 ? hist_lane_batch_kernel<T, false, true>
+                                                        : hist_lane_batch_kernel<T, false, false>);
+    const size_t smem = size_t(nbins) * 32 * 4;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHistThreads, smem) != cudaSuccess)
+        return MCTP_ECUDA;
+    per_sm = std::max(per_sm, 1);
+    constexpr int E = 16 / sizeof(T);
+    for (int base = 0; base < count; base += kHistBatch) {
+        HistBatch b{};
+        b.count = std::min(kHistBatch, count - base);
+        b.nbins = nbins;
+        b.shift = shift;
+        b.limit = bits >= 32 ? 0xffffffffu : (1u << bits);
+        b.hist = reinterpret_cast<unsigned long long *>(hist + int64_t(base) * nbins);
+        b.overflow = reinterpret_cast<unsigned long long *>(overflow + base);
+        for (int i = 0; i < b.count; ++i) {
+            const mctp_volume_desc &d = descs[base + i];
+            const int64_t n = d.nx * d.ny * d.nz;
+            const uintptr_t addr = reinterpret_cast<uintptr_t>(vols[base + i]);
+            const int64_t head = std::min<int64_t>(int64_t(((16 - (addr & 15)) & 15) / sizeof(T)), n);
+            b.vol[i] = vols[base + i];
+            b.n[i] = n;
+            b.head[i] = int32_t(head);
+            b.first[i + 1] = b.first[i] + (n - head) / E;
+        }
+        const int64_t total = b.first[b.count];
+        int64_t grid = std::min<int64_t>(int64_t(per_sm) * num_sms(),
+                                         std::max<int64_t>((total + kHistThreads * kHistUnroll - 1) /
+                                                               (kHistThreads * kHistUnroll), b.count));
+        // every lane counter of a block stays below 2^31
+        grid = std::max<int64_t>(grid, (total >> 36) + 1);
+        grid = std::min<int64_t>(std::max<int64_t>(grid, 1), 0x7fffffff);
+        kern<<<unsigned(grid), kHistThreads, smem, s>>>(b);
+        const int rc = launch_status();
+        if (rc != MCTP_OK) return rc;
+    }
+    return MCTP_OK;
+}
+
 }  // namespace
 
 MCTP_FAULT_READER(hist)
@@ -332,4 +496,34 @@ extern "C" int mctp_build_histogram(const void *vol, const mctp_volume_desc *d, 
     if (d->dtype == MCTP_U8)
         return launch_hist(static_cast<const uint8_t *>(vol) + z0 * plane, n, d->bits, nbins, hist, overflow, s);
     return launch_hist(static_cast<const uint16_t *>(vol) + z0 * plane, n, d->bits, nbins, hist, overflow, s);
+}
+
+extern "C" int mctp_build_histogram_batch(const void *const *vols, const mctp_volume_desc *descs, int32_t count,
+                                          int32_t nbins, uint64_t *hist, uint64_t *overflow, void *stream)
+{
+    using namespace mctp;
+    if (count < 0 || (count > 0 && (!vols || !descs || !hist || !overflow))) return MCTP_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const int rc = check_desc(&descs[i]);
+        if (rc != MCTP_OK) return rc;
+        if (!vols[i]) return MCTP_EINVAL;
+        if (descs[i].dtype != descs[0].dtype || descs[i].bits != descs[0].bits) return MCTP_EINVAL;
+    }
+    if (count == 0) return MCTP_OK;
+    if (bin_shift(descs[0].bits, nbins) < 0) return MCTP_EINVAL;
+    if (int64_t(count) * nbins > (int64_t(1) << 40)) return MCTP_EINVAL;
+    if (nbins > 256) {  // one launch per volume (the window kernel)
+        for (int i = 0; i < count; ++i) {
+            const int rc = mctp_build_histogram(vols[i], &descs[i], 0, descs[i].nz, nbins, hist + int64_t(i) * nbins,
+                                                overflow + i, stream);
+            if (rc != MCTP_OK) return rc;
+        }
+        return MCTP_OK;
+    }
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(hist, 0, size_t(count) * size_t(nbins) * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(overflow, 0, size_t(count) * sizeof(uint64_t), s) != cudaSuccess)
+        return MCTP_ECUDA;
+    if (descs[0].dtype == MCTP_U8) return launch_hist_batch<uint8_t>(vols, descs, count, nbins, hist, overflow, s);
+    return launch_hist_batch<uint16_t>(vols, descs, count, nbins, hist, overflow, s);
 }

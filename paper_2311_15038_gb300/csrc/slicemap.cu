@@ -28,8 +28,12 @@
 // When the keep table is a step (keep[b] = b >= T, as Otsu, ITS and explicit
 // thresholds produce) the per-voxel table lookup becomes one comparison.
 // A single u8 level from rows of at most 1024 bytes (many small volumes) takes
-// a warp-per-row kernel instead (slicemap_rows_u8_kernel below).
+// a warp-per-row kernel instead (slicemap_rows_u8_kernel below), which sums
+// bytes as exact fp16 pairs and reduces x through prefix sums.
 #include <algorithm>
+
+#include <cuda_fp16.h>
+#include <string.h>
 
 #include "slicemap_common.cuh"
 
@@ -347,17 +351,21 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
 //
 // One warp per level-0 row (z, y) at a time, persistent warps, no CTA barrier
 // in the loop.  Lane l owns source columns [32 l, 32 l + 32): for each source
-// row of the footprint it loads the three aligned 16-byte chunks around its 32
-// bytes (any row alignment), funnel-shifts them into place and adds the bytes
-// into packed 16-bit column sums (kept values only); the warp then writes its
-// column sums to its own shared row and each lane takes output columns x =
-// lane, lane + 32, ... : the sum over the x footprint, divided and rounded.
-// The x, y and z footprint tables and the keep table are set up once per
-// block.
+// row of the footprint it loads the aligned 16-byte chunks around its 32
+// bytes (any row alignment), funnel-shifts them into place and adds the kept
+// bytes into column sums.  For a step keep table (or none) the sums are fp16
+// pairs: byte b is the fp16 value b 2^-24, the sum of up to 8 bytes is exact,
+// and an fp16 value k 2^-24 with integer k <= 2048 has the bit pattern k, so
+// the pair registers are at the same time packed 16-bit column sums; they are
+// folded into the warp's shared row after every 8 source rows.  A general
+// keep table adds bytes into packed 16-bit integer sums.  The warp then turns
+// the row's column sums into exclusive prefix sums E (a scan within each lane
+// and across the warp), and output voxel x takes E[c1] - E[c0] over its
+// footprint [c0, c1), divided and rounded.
 constexpr int kRowsWarps = 8;
-constexpr int kRowsMaxCols = 1024;                             // source row bytes the kernel takes
-constexpr int kRowsMaxYZ = 4096;                               // level rows / slices the tables take
-constexpr int kRowsColsPad = kRowsMaxCols + kRowsMaxCols / 4;  // u16 per warp row: 8 of padding per 32
+constexpr int kRowsMaxCols = 1024;     // source row bytes the kernel takes
+constexpr int kRowsMaxYZ = 4096;       // level rows / slices the tables take
+constexpr int kRowsScratch = 1028;     // u32 per warp: column sums (80 B per lane), then E[0..nx] from word 3
 
 struct RowsArgs {
     const uint8_t *vol;
@@ -430,8 +438,131 @@ __device__ __forceinline__ void add_vector_u8_lut(const uint4 &q, uint32_t *acc,
     }
 }
 
-// floor((sum + cnt / 2) / cnt) for a quotient of at most a few hundred: a float
-// estimate and one correction step each way.
+__device__ __forceinline__ __half2 bits_h2(uint32_t u)
+{
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h)
+{
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+// 16 bytes into fp16 pair sums: acc[2 k] gets bytes 0, 2 of word k, acc[2 k + 1]
+// bytes 1, 3; with a step table (mode 2) only bytes >= thr (the pair value of
+// the lowest kept byte).
+template <int kMode>
+__device__ __forceinline__ void add_vector_u8_h2(const uint4 &q, __half2 *acc, __half2 thr)
+{
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t e, o;
+        asm("prmt.b32 %0, %1, 0, 0x4240;" : "=r"(e) : "r"(w[k]));
+        asm("prmt.b32 %0, %1, 0, 0x4341;" : "=r"(o) : "r"(w[k]));
+        const __half2 he = bits_h2(e), ho = bits_h2(o);
+        if (kMode == 2) {
+            acc[2 * k] = __hfma2(he, __hge2(he, thr), acc[2 * k]);
+            acc[2 * k + 1] = __hfma2(ho, __hge2(ho, thr), acc[2 * k + 1]);
+        } else {
+            acc[2 * k] = __hadd2(acc[2 * k], he);
+            acc[2 * k + 1] = __hadd2(acc[2 * k + 1], ho);
+        }
+    }
+}
+
+// Even/odd pair sums of 32 columns (acc[8 g + 2 k]: columns 16 g + 4 k + {0, 2},
+// acc[8 g + 2 k + 1]: + {1, 3}) as 16 words of consecutive column pairs, stored
+// or added into dst.
+__device__ __forceinline__ void store_columns(const uint32_t *acc, uint4 *dst, bool add)
+{
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t ev = acc[8 * g + 2 * k], od = acc[8 * g + 2 * k + 1];
+            asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(w[2 * k]) : "r"(ev), "r"(od));
+            asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w[2 * k + 1]) : "r"(ev), "r"(od));
+        }
+        uint4 v0 = make_uint4(w[0], w[1], w[2], w[3]), v1 = make_uint4(w[4], w[5], w[6], w[7]);
+        if (add) {
+            const uint4 o0 = dst[2 * g], o1 = dst[2 * g + 1];
+            v0 = make_uint4(v0.x + o0.x, v0.y + o0.y, v0.z + o0.z, v0.w + o0.w);
+            v1 = make_uint4(v1.x + o1.x, v1.y + o1.y, v1.z + o1.z, v1.w + o1.w);
+        }
+        dst[2 * g] = v0;
+        dst[2 * g + 1] = v1;
+    }
+}
+
+// Column sums of a level row's footprint into the lane's 32 columns of dst.
+template <int kMode>
+__device__ __forceinline__ void rows_accumulate(const RowsArgs &a, const uint8_t *lut, __half2 thr, int zlo, int ylo,
+                                                int wy, int R, int lane, uint4 *dst)
+{
+    const int64_t nx = a.nx;
+    const char *rs = reinterpret_cast<const char *>(a.vol) + (int64_t(zlo) * a.ny + ylo) * nx;
+    const int64_t slice_jump = (a.ny - wy + 1) * nx;
+    int yi = 0;
+    auto next_row = [&]() {
+        const char *r = rs;
+        if (++yi == wy) { yi = 0; rs += slice_jump; } else { rs += nx; }
+        return r;
+    };
+    if constexpr (kMode == 1) {
+        uint32_t acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = 0u;
+        for (int r = 0; r < R; r += 2) {
+            uint4 q[4];
+            const char *r1 = next_row();
+            load_lane32(r1 + 32 * lane, r1 + nx, q[0], q[1]);
+            if (r + 1 < R) {
+                const char *r2 = next_row();
+                load_lane32(r2 + 32 * lane, r2 + nx, q[2], q[3]);
+            } else {
+                q[2] = q[3] = make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add_vector_u8_lut(q[u], acc + 8 * (u & 1), lut, a.shift);
+        }
+        store_columns(acc, dst, false);
+    } else {
+    for (int r = 0; r < R;) {
+        __half2 h[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) h[e] = bits_h2(0u);
+        const int first = r;
+        const int rend = min(R, r + 8);  // 8 rows of bytes sum to at most 2040: exact in fp16
+        for (; r < rend; r += 2) {
+            uint4 q[4];
+            const char *r1 = next_row();
+            load_lane32(r1 + 32 * lane, r1 + nx, q[0], q[1]);
+            if (r + 1 < rend) {
+                const char *r2 = next_row();
+                load_lane32(r2 + 32 * lane, r2 + nx, q[2], q[3]);
+            } else {
+                q[2] = q[3] = make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add_vector_u8_h2<kMode>(q[u], h + 8 * (u & 1), thr);
+        }
+        uint32_t acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = h2_bits(h[e]);
+        store_columns(acc, dst, first > 0);
+    }
+    }
+}
+
+// floor((sum + cnt / 2) / cnt) for a quotient of at most a few hundred, from
+// an approximate reciprocal of cnt: the estimate is within one of the
+// quotient, and one correction step each way makes it exact.
 __device__ __forceinline__ uint32_t div_round(uint32_t sum, uint32_t cnt, float rcp)
 {
     const uint32_t n = sum + cnt / 2u;
@@ -441,32 +572,11 @@ __device__ __forceinline__ uint32_t div_round(uint32_t sum, uint32_t cnt, float 
     return q;
 }
 
-template <int kMode>
-__device__ __forceinline__ void rows_accumulate(const RowsArgs &a, const uint8_t *lut, uint32_t k_fast, int zlo,
-                                                int ylo, int wy, int R, int lane, uint32_t acc[16])
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    const int64_t nx = a.nx;
-    const char *rs = reinterpret_cast<const char *>(a.vol) + (int64_t(zlo) * a.ny + ylo) * nx;
-    const int64_t slice_jump = (a.ny - wy + 1) * nx;
-    int yi = 0;
-    for (int r = 0; r < R; r += 2) {
-        uint4 q[4];
-        const char *r1 = rs;
-        if (++yi == wy) { yi = 0; rs += slice_jump; } else { rs += nx; }
-        load_lane32(r1 + 32 * lane, r1 + nx, q[0], q[1]);
-        if (r + 1 < R) {
-            const char *r2 = rs;
-            if (++yi == wy) { yi = 0; rs += slice_jump; } else { rs += nx; }
-            load_lane32(r2 + 32 * lane, r2 + nx, q[2], q[3]);
-        } else {
-            q[2] = q[3] = make_uint4(0u, 0u, 0u, 0u);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (kMode == 1) add_vector_u8_lut(q[u], acc + 8 * (u & 1), lut, a.shift);
-            else add_vector_u8_packed<kMode>(q[u], acc + 8 * (u & 1), k_fast);
-        }
-    }
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(const __grid_constant__ RowsArgs a)
@@ -476,8 +586,8 @@ __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(co
     int32_t *yb = xb + a.mx + 1;                           // my + 1
     int32_t *zb = yb + a.my + 1;                           // mz + 1
     const int ntab = a.mx + a.my + a.mz + 3;
-    uint16_t *cols = reinterpret_cast<uint16_t *>(smem_rows + ((size_t(ntab) * 4 + 15) / 16) * 16);
-    uint8_t *lut = reinterpret_cast<uint8_t *>(cols + kRowsWarps * kRowsColsPad);
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(smem_rows + ((size_t(ntab) * 4 + 15) / 16) * 16);
+    uint8_t *lut = reinterpret_cast<uint8_t *>(scratch + kRowsWarps * kRowsScratch);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i <= a.mx; i += blockDim.x) xb[i] = int32_t((int64_t(i) * a.nx) / a.mx);
     for (int i = threadIdx.x; i <= a.my; i += blockDim.x) yb[i] = int32_t((int64_t(i) * a.ny) / a.my);
@@ -487,48 +597,72 @@ __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(co
     const int mode = load_keep_table(a.keep, a.nbins, a.shift, a.limit, lut, sh_keep, int(threadIdx.x),
                                      int(blockDim.x), &lo, [] { __syncthreads(); });
     __syncthreads();
-    const uint32_t k_fast = (0x8000u - lo) * 0x00010001u;
-    uint16_t *mine = cols + warp * kRowsColsPad;
+    // the fp16 pair of the lowest kept byte (bit pattern lo, see above)
+    const __half2 thr = bits_h2(lo | (lo << 16));
+    uint32_t *mine = scratch + warp * kRowsScratch;
+    uint4 *cols = reinterpret_cast<uint4 *>(mine) + 5 * lane;  // this lane's 32 column sums (80 bytes)
+    uint32_t *E = mine + 3;                                      // E[c], c = 0..nx; E + 4 is 16-byte aligned
     const int64_t nrows = int64_t(a.mz) * a.my;
     const int64_t nwarps = int64_t(gridDim.x) * kRowsWarps;
     const bool active = 32 * lane < a.nx;
-    for (int64_t row = int64_t(blockIdx.x) * kRowsWarps + warp; row < nrows; row += nwarps) {
-        const int z = int(row / a.my), y = int(row - int64_t(z) * a.my);
+    const int wlo = int(a.nx / a.mx);  // footprint widths along x are wlo or wlo + 1
+    const int64_t first_row = int64_t(blockIdx.x) * kRowsWarps + warp;
+    const int step_z = int(nwarps / a.my), step_y = int(nwarps - int64_t(step_z) * a.my);
+    int z = int(first_row / a.my), y = int(first_row - int64_t(z) * a.my);
+    for (int64_t row = first_row; row < nrows; row += nwarps) {
         const int zlo = zb[z], ylo = yb[y];
         const int wy = yb[y + 1] - ylo, R = (zb[z + 1] - zlo) * wy;
-        uint32_t acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0u;
         if (active) {
-            if (mode == 0) rows_accumulate<0>(a, lut, k_fast, zlo, ylo, wy, R, lane, acc);
-            else if (mode == 1) rows_accumulate<1>(a, lut, k_fast, zlo, ylo, wy, R, lane, acc);
-            else rows_accumulate<2>(a, lut, k_fast, zlo, ylo, wy, R, lane, acc);
+            if (mode == 0) rows_accumulate<0>(a, lut, thr, zlo, ylo, wy, R, lane, cols);
+            else if (mode == 1) rows_accumulate<1>(a, lut, thr, zlo, ylo, wy, R, lane, cols);
+            else rows_accumulate<2>(a, lut, thr, zlo, ylo, wy, R, lane, cols);
         }
-        // column sums of columns 32 lane + 16 h + 4 k + j as u16, 8 of padding per 32 columns
-        uint4 *dst = reinterpret_cast<uint4 *>(mine + 40 * lane);
+        __syncwarp();
+        // exclusive prefix sums of the row's columns (E[32 l + j + 1] from lane l)
+        uint32_t v[16];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t w[8];
+        for (int g = 0; g < 4; ++g) {
+            const uint4 t = cols[g];
+            v[4 * g] = t.x; v[4 * g + 1] = t.y; v[4 * g + 2] = t.z; v[4 * g + 3] = t.w;
+        }
+        uint32_t total = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t ev = acc[8 * h + 2 * k], od = acc[8 * h + 2 * k + 1];
-                asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(w[2 * k]) : "r"(ev), "r"(od));
-                asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w[2 * k + 1]) : "r"(ev), "r"(od));
+        for (int i = 0; i < 16; ++i) total += (v[i] & 0xffffu) + (v[i] >> 16);
+        uint32_t incl = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        __syncwarp();
+        uint32_t run = incl - total;
+        if (lane == 0) E[0] = 0u;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            uint32_t p[4];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                run += v[2 * g + k] & 0xffffu;
+                p[2 * k] = run;
+                run += v[2 * g + k] >> 16;
+                p[2 * k + 1] = run;
             }
-            dst[2 * h] = make_uint4(w[0], w[1], w[2], w[3]);
-            dst[2 * h + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+            reinterpret_cast<uint4 *>(E + 1 + 32 * lane)[g] = make_uint4(p[0], p[1], p[2], p[3]);
         }
         __syncwarp();
         uint8_t *out = atlas_ptr(a.atlas, a.pitch, a.tiles_x, a.mx, a.my, 0, y, z);
+        const float rcp_lo = rcp_approx(float(wlo * R)), rcp_hi = rcp_approx(float((wlo + 1) * R));
         for (int x = lane; x < a.mx; x += 32) {
             const int c0 = xb[x], c1 = xb[x + 1];
-            uint32_t sum = 0;
-            for (int c = c0; c < c1; ++c) sum += mine[c + (c >> 5) * 8];
-            const uint32_t cnt = uint32_t(c1 - c0) * uint32_t(R);
-            if (in_range((out - a.atlas) + x, a.elems, kFaultAtlasWrite))
-                out[x] = uint8_t(div_round(sum, cnt, 1.0f / float(cnt)));
+            const uint32_t sum = E[c1] - E[c0];
+            const int w = c1 - c0;
+            const uint32_t q = div_round(sum, uint32_t(w * R), w == wlo ? rcp_lo : rcp_hi);
+            if (in_range((out - a.atlas) + x, a.elems, kFaultAtlasWrite)) out[x] = uint8_t(q);
         }
         __syncwarp();
+        y += step_y;
+        z += step_z;
+        if (y >= a.my) { y -= a.my; ++z; }
     }
 }
 
@@ -563,13 +697,14 @@ __global__ void __launch_bounds__(256) halve_kernel(const T *__restrict__ src, i
 // maxima of its x positions over the cell rows' 9 x 9 (y, z) atlas rows,
 // loading the 9 rows of a slice together, then each cell takes the maximum of
 // its 9 columns from shared memory.
+// Block `block` of a level's max grid: cell row (cz, cy) = (block / gy, block % gy).
 template <typename T>
-__global__ void __launch_bounds__(256) maxgrid_kernel(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx,
-                                                      int my, int mz, uint16_t *__restrict__ grid, int gx, int gy)
+__device__ __forceinline__ void maxgrid_row(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx, int my,
+                                            int mz, uint16_t *__restrict__ grid, int gx, int gy, int block,
+                                            uint32_t *colmax)
 {
-    extern __shared__ uint32_t colmax[];
     constexpr int c = MCTP_MAXGRID_CELL;
-    const int cy = blockIdx.x % gy, cz = blockIdx.x / gy;
+    const int cy = block % gy, cz = block / gy;
     const int z1 = min(cz * c + c, mz - 1), y0 = cy * c, ny_rows = min(cy * c + c, my - 1) - y0 + 1;
     for (int x = threadIdx.x; x < mx; x += blockDim.x) {
         uint32_t m = 0;
@@ -590,6 +725,45 @@ __global__ void __launch_bounds__(256) maxgrid_kernel(const T *__restrict__ atla
         for (int x = cx * c; x <= x1; ++x) m = max(m, colmax[x]);
         grid[(int64_t(cz) * gy + cy) * gx + cx] = uint16_t(m);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) maxgrid_kernel(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx,
+                                                      int my, int mz, uint16_t *__restrict__ grid, int gx, int gy)
+{
+    extern __shared__ uint32_t colmax[];
+    maxgrid_row<T>(atlas, pitch, tiles_x, mx, my, mz, grid, gx, gy, int(blockIdx.x), colmax);
+}
+
+// The max grids of up to kGridBatch levels (of one element type) in one
+// launch: item i owns blocks [first[i], first[i + 1]).  Many small volumes
+// then share one launch instead of one short launch each.
+constexpr int kGridBatch = 64;
+struct MaxgridItem {
+    const void *atlas;
+    uint16_t *grid;
+    int64_t pitch;
+    int32_t tiles_x, mx, my, mz, gx, gy;
+};
+struct MaxgridBatch {
+    int32_t count;
+    int32_t first[kGridBatch + 1];
+    MaxgridItem item[kGridBatch];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) maxgrid_batch_kernel(const __grid_constant__ MaxgridBatch b)
+{
+    extern __shared__ uint32_t colmax[];
+    int lo = 0, hi = b.count - 1;  // the item whose block range holds blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.first[mid] <= int(blockIdx.x)) lo = mid;
+        else hi = mid - 1;
+    }
+    const MaxgridItem &it = b.item[lo];
+    maxgrid_row<T>(static_cast<const T *>(it.atlas), it.pitch, it.tiles_x, it.mx, it.my, it.mz, it.grid, it.gx,
+                   it.gy, int(blockIdx.x) - b.first[lo], colmax);
 }
 
 // Zero the tiles of an atlas that hold no slice.
@@ -628,7 +802,7 @@ int launch_maxgrid(const mctp_slicemap *sm, int k, cudaStream_t s)
 
 template <typename T>
 int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep, int nbins, const mctp_slicemap *sm,
-                    cudaStream_t s)
+                    cudaStream_t s, bool maxgrids = true)
 {
     int rc = MCTP_OK;
     int done_levels = 0;   // levels 1..done_levels written by the level-0 kernel
@@ -650,7 +824,7 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
         a.shift = keep ? bin_shift(d->bits, nbins) : 0;
         a.limit = 1u << d->bits;
         const size_t smem = ((size_t(a.mx + a.my + a.mz + 3) * 4 + 15) / 16) * 16 +
-                            size_t(kRowsWarps) * kRowsColsPad * 2 + (keep ? size_t(nbins) : 0);
+                            size_t(kRowsWarps) * kRowsScratch * 4 + (keep ? size_t(nbins) : 0);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(slicemap_rows_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
                 cudaSuccess)
@@ -728,12 +902,56 @@ int launch_slicemap(const T *vol, const mctp_volume_desc *d, const uint8_t *keep
                                sm->tiles_x[k], sm->tiles_y[k], s);
         if (rc != MCTP_OK) return rc;
     }
-    for (int k = 0; k < sm->nlevels; ++k) {
+    for (int k = 0; maxgrids && k < sm->nlevels; ++k) {
         if (!sm->maxgrid[k]) continue;
         rc = launch_maxgrid<T>(sm, k, s);
         if (rc != MCTP_OK) return rc;
     }
     return MCTP_OK;
+}
+
+// The max grids of every level of sms[0..count) that has one, kGridBatch
+// levels per launch.
+template <typename T>
+int launch_maxgrid_batch(const mctp_slicemap *sms, int count, cudaStream_t s)
+{
+    MaxgridBatch b{};
+    size_t smem = 0;
+    auto flush = [&]() -> int {
+        if (b.count == 0) return MCTP_OK;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(maxgrid_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+                cudaSuccess)
+            return MCTP_ECUDA;
+        maxgrid_batch_kernel<T><<<unsigned(b.first[b.count]), 256, smem, s>>>(b);
+        b.count = 0;
+        smem = 0;
+        return launch_status();
+    };
+    for (int i = 0; i < count; ++i) {
+        const mctp_slicemap *sm = &sms[i];
+        for (int k = 0; k < sm->nlevels; ++k) {
+            if (!sm->maxgrid[k]) continue;
+            const int c = MCTP_MAXGRID_CELL;
+            const int mx = sm->dims[k][0], my = sm->dims[k][1], mz = sm->dims[k][2];
+            const int gx = (mx + c - 1) / c, gy = (my + c - 1) / c, gz = (mz + c - 1) / c;
+            if (size_t(mx) * sizeof(uint32_t) > 200 * 1024) return MCTP_EUNSUPPORTED;
+            if (b.count == kGridBatch || int64_t(b.first[b.count]) + int64_t(gy) * gz > 0x7fffffff) {
+                const int rc = flush();
+                if (rc != MCTP_OK) return rc;
+            }
+            MaxgridItem &it = b.item[b.count];
+            it.atlas = sm->atlas[k];
+            it.grid = static_cast<uint16_t *>(sm->maxgrid[k]);
+            it.pitch = int64_t(sm->tiles_x[k]) * mx;
+            it.tiles_x = sm->tiles_x[k];
+            it.mx = mx; it.my = my; it.mz = mz; it.gx = gx; it.gy = gy;
+            b.first[b.count + 1] = b.first[b.count] + gy * gz;
+            ++b.count;
+            smem = std::max(smem, size_t(mx) * sizeof(uint32_t));
+        }
+    }
+    return flush();
 }
 
 }  // namespace
@@ -766,10 +984,11 @@ MCTP_FAULT_READER(slicemap)
 
 }  // namespace mctp
 
-extern "C" int mctp_build_slicemap(const void *vol, const mctp_volume_desc *d, const uint8_t *keep_lut,
-                                   int32_t nbins, const mctp_slicemap *sm, void *stream)
+namespace mctp {
+namespace {
+int check_build(const void *vol, const mctp_volume_desc *d, const uint8_t *keep_lut, int32_t nbins,
+                const mctp_slicemap *sm)
 {
-    using namespace mctp;
     int rc = check_desc(d);
     if (rc != MCTP_OK) return rc;
     rc = check_slicemap(sm);
@@ -784,8 +1003,47 @@ extern "C" int mctp_build_slicemap(const void *vol, const mctp_volume_desc *d, c
     const int64_t n3[3] = {d->nx, d->ny, d->nz};
     for (int a = 0; a < 3; ++a) fp *= (n3[a] + sm->dims[0][a] - 1) / sm->dims[0][a];
     if (fp * ((int64_t(1) << d->bits) - 1) >= (int64_t(1) << 32)) return MCTP_EUNSUPPORTED;
+    return MCTP_OK;
+}
+}  // namespace
+}  // namespace mctp
+
+extern "C" int mctp_build_slicemap(const void *vol, const mctp_volume_desc *d, const uint8_t *keep_lut,
+                                   int32_t nbins, const mctp_slicemap *sm, void *stream)
+{
+    using namespace mctp;
+    const int rc = check_build(vol, d, keep_lut, nbins, sm);
+    if (rc != MCTP_OK) return rc;
     cudaStream_t s = as_stream(stream);
     if (d->dtype == MCTP_U8)
         return launch_slicemap(static_cast<const uint8_t *>(vol), d, keep_lut, nbins, sm, s);
     return launch_slicemap(static_cast<const uint16_t *>(vol), d, keep_lut, nbins, sm, s);
+}
+
+extern "C" int mctp_build_slicemap_batch(const void *const *vols, const mctp_volume_desc *descs,
+                                         const uint8_t *keep_luts, int32_t nbins, const mctp_slicemap *sms,
+                                         int32_t count, void *stream)
+{
+    using namespace mctp;
+    if (count < 0 || (count > 0 && (!vols || !descs || !sms))) return MCTP_EINVAL;
+    if (count == 0) return MCTP_OK;
+    if (keep_luts && (nbins < 1 || int64_t(count) * nbins > (int64_t(1) << 40))) return MCTP_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const int rc = check_build(vols[i], &descs[i], keep_luts ? keep_luts + int64_t(i) * nbins : nullptr, nbins,
+                                   &sms[i]);
+        if (rc != MCTP_OK) return rc;
+        if (descs[i].dtype != descs[0].dtype) return MCTP_EINVAL;
+    }
+    cudaStream_t s = as_stream(stream);
+    for (int i = 0; i < count; ++i) {
+        const uint8_t *keep = keep_luts ? keep_luts + int64_t(i) * nbins : nullptr;
+        const int rc = descs[i].dtype == MCTP_U8
+                           ? launch_slicemap(static_cast<const uint8_t *>(vols[i]), &descs[i], keep, nbins, &sms[i], s,
+                                             false)
+                           : launch_slicemap(static_cast<const uint16_t *>(vols[i]), &descs[i], keep, nbins, &sms[i],
+                                             s, false);
+        if (rc != MCTP_OK) return rc;
+    }
+    return descs[0].dtype == MCTP_U8 ? launch_maxgrid_batch<uint8_t>(sms, count, s)
+                                     : launch_maxgrid_batch<uint16_t>(sms, count, s);
 }

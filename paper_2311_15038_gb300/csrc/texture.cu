@@ -32,32 +32,37 @@ namespace {
 
 constexpr int kSurfThreads = 512;
 
-// Row Y = blockIdx.x of the padded array.  The block stages its atlas row
-// (the row ly of tile row `row`) in shared memory, with 16-byte loads when
-// the row is 16-byte aligned, then writes the padded row: texel X of cell
-// (col, row) holds atlas texel (col mx + lx, ...) with lx = X - col (mx + 2) - 1
-// clamped to the tile.  Consecutive threads store consecutive texels; the
-// cell of X comes from a float estimate (X < 2^16 is exact) and one
-// correction.
+// Rows Y0 .. Y0 + rows_per_block - 1 of a padded array (Y0 = block x
+// rows_per_block; several short rows per block keep more loads in flight).
+// The block stages each row's atlas row (the row ly of tile row `row`) in
+// shared memory, with 16-byte loads when the row is 16-byte aligned, then
+// writes the padded rows: texel X of cell (col, row) holds atlas texel
+// (col mx + lx, ...) with lx = X - col (mx + 2) - 1 clamped to the tile.
+// Consecutive threads store consecutive texels; the cell of X comes from a
+// float estimate (X < 2^16 is exact) and one correction.
 template <typename T>
-__global__ void __launch_bounds__(kSurfThreads) atlas_pad_kernel(const T *__restrict__ atlas, int64_t pitch,
-                                                                 int32_t mx, int32_t my, int32_t width,
-                                                                 cudaSurfaceObject_t surf)
+__device__ __forceinline__ void pad_rows(const T *__restrict__ atlas, int64_t pitch, int32_t mx, int32_t my,
+                                         int32_t width, cudaSurfaceObject_t surf, int32_t height,
+                                         int32_t rows_per_block, int block, unsigned char *sh_row_bytes)
 {
-    extern __shared__ __align__(16) unsigned char sh_row_bytes[];
-    T *sh_row = reinterpret_cast<T *>(sh_row_bytes);
-    const int Y = blockIdx.x;
-    const int row = Y / (my + 2);
-    const int ly = min(max(Y - row * (my + 2) - 1, 0), my - 1);
-    const T *src = atlas + (int64_t(row) * my + ly) * pitch;
     constexpr int E = 16 / int(sizeof(T));
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-        const uint4 *v = reinterpret_cast<const uint4 *>(src);
-        const int nvec = int(pitch / E);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) reinterpret_cast<uint4 *>(sh_row)[i] = __ldg(v + i);
-        for (int i = nvec * E + threadIdx.x; i < pitch; i += blockDim.x) sh_row[i] = __ldg(src + i);
-    } else {
-        for (int i = threadIdx.x; i < pitch; i += blockDim.x) sh_row[i] = __ldg(src + i);
+    const int Y0 = block * rows_per_block;
+    const int nrows = min(rows_per_block, height - Y0);
+    const int64_t stride = (pitch + E - 1) / E * E;  // staged row stride in elements (16-byte multiple)
+    for (int k = 0; k < nrows; ++k) {
+        const int Y = Y0 + k;
+        T *sh_row = reinterpret_cast<T *>(sh_row_bytes) + k * stride;
+        const int row = Y / (my + 2);
+        const int ly = min(max(Y - row * (my + 2) - 1, 0), my - 1);
+        const T *src = atlas + (int64_t(row) * my + ly) * pitch;
+        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const uint4 *v = reinterpret_cast<const uint4 *>(src);
+            const int nvec = int(pitch / E);
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) reinterpret_cast<uint4 *>(sh_row)[i] = __ldg(v + i);
+            for (int i = nvec * E + threadIdx.x; i < pitch; i += blockDim.x) sh_row[i] = __ldg(src + i);
+        } else {
+            for (int i = threadIdx.x; i < pitch; i += blockDim.x) sh_row[i] = __ldg(src + i);
+        }
     }
     __syncthreads();
     const int cw = mx + 2;
@@ -67,8 +72,46 @@ __global__ void __launch_bounds__(kSurfThreads) atlas_pad_kernel(const T *__rest
         if (col * cw > X) --col;
         else if ((col + 1) * cw <= X) ++col;
         const int lx = min(max(X - col * cw - 1, 0), mx - 1);
-        surf2Dwrite<T>(sh_row[col * mx + lx], surf, X * int(sizeof(T)), Y, cudaBoundaryModeZero);
+        for (int k = 0; k < nrows; ++k)
+            surf2Dwrite<T>(reinterpret_cast<T *>(sh_row_bytes)[k * stride + col * mx + lx], surf, X * int(sizeof(T)),
+                           Y0 + k, cudaBoundaryModeZero);
     }
+}
+
+// Up to kPadBatch textures (of one element type) in one launch: item i owns
+// blocks [first[i], first[i + 1]).
+constexpr int kPadBatch = 64;
+struct PadItem {
+    const void *atlas;
+    cudaSurfaceObject_t surf;
+    int64_t pitch;
+    int32_t mx, my, width, height, rows_per_block;
+};
+struct PadBatch {
+    int32_t count;
+    int32_t first[kPadBatch + 1];
+    PadItem item[kPadBatch];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kSurfThreads) atlas_pad_batch_kernel(const __grid_constant__ PadBatch b)
+{
+    extern __shared__ __align__(16) unsigned char sh_row_bytes[];
+    int lo = 0, hi = b.count - 1;  // the item whose block range holds blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.first[mid] <= int(blockIdx.x)) lo = mid;
+        else hi = mid - 1;
+    }
+    const PadItem &it = b.item[lo];
+    pad_rows<T>(static_cast<const T *>(it.atlas), it.pitch, it.mx, it.my, it.width, it.surf, it.height,
+                it.rows_per_block, int(blockIdx.x) - b.first[lo], sh_row_bytes);
+}
+
+// Rows per block for staged rows of row_bytes: up to 4 while they fit 48 KB.
+int pad_rows_per_block(size_t row_bytes)
+{
+    return int(std::max<size_t>(1, std::min<size_t>(4, (48 * 1024) / row_bytes)));
 }
 
 int texture_geometry(const mctp_slicemap *sm, int32_t level, int64_t &w, int64_t &h)
@@ -142,8 +185,9 @@ extern "C" int mctp_atlas_texture_create(const mctp_slicemap *sm, int32_t level,
     return MCTP_OK;
 }
 
-extern "C" int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slicemap *sm, int32_t level,
-                                         void *stream)
+namespace {
+// The texture t was made for this level's geometry.
+int check_update(const mctp_atlas_texture *t, const mctp_slicemap *sm, int32_t level)
 {
     if (!t) return MCTP_EINVAL;
     int64_t w = 0, h = 0;
@@ -152,24 +196,75 @@ extern "C" int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slice
     if (w != t->width || h != t->height || sm->dtype != t->dtype || sm->dims[level][0] != t->mx ||
         sm->dims[level][1] != t->my || sm->tiles_x[level] != t->tiles_x || sm->tiles_y[level] != t->tiles_y)
         return MCTP_EINVAL;
-    cudaStream_t s = mctp::as_stream(stream);
-    const int64_t pitch = int64_t(sm->tiles_x[level]) * sm->dims[level][0];
-    const size_t smem = size_t(pitch) * size_t(mctp::elem_size(sm->dtype));
-    auto kern = sm->dtype == MCTP_U8 ? reinterpret_cast<const void *>(atlas_pad_kernel<uint8_t>)
-                                     : reinterpret_cast<const void *>(atlas_pad_kernel<uint16_t>);
-    if (smem > 200 * 1024) return MCTP_ESIZE;
+    return MCTP_OK;
+}
+
+template <typename T>
+int launch_pad_batch(const PadBatch &b, size_t smem, cudaStream_t s)
+{
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        cudaFuncSetAttribute(atlas_pad_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess)
         return MCTP_ECUDA;
-    if (sm->dtype == MCTP_U8)
-        atlas_pad_kernel<uint8_t><<<unsigned(h), kSurfThreads, smem, s>>>(
-            static_cast<const uint8_t *>(sm->atlas[level]), pitch, sm->dims[level][0], sm->dims[level][1], int32_t(w),
-            t->surf);
-    else
-        atlas_pad_kernel<uint16_t><<<unsigned(h), kSurfThreads, smem, s>>>(
-            static_cast<const uint16_t *>(sm->atlas[level]), pitch, sm->dims[level][0], sm->dims[level][1],
-            int32_t(w), t->surf);
+    atlas_pad_batch_kernel<T><<<unsigned(b.first[b.count]), kSurfThreads, smem, s>>>(b);
     return mctp::launch_status();
+}
+}  // namespace
+
+extern "C" int mctp_atlas_texture_update(mctp_atlas_texture *t, const mctp_slicemap *sm, int32_t level,
+                                         void *stream)
+{
+    return mctp_atlas_texture_update_batch(&t, sm, &level, 1, stream);
+}
+
+extern "C" int mctp_atlas_texture_update_batch(mctp_atlas_texture *const *textures, const mctp_slicemap *sms,
+                                               const int32_t *levels, int32_t count, void *stream)
+{
+    if (count < 0 || (count > 0 && (!textures || !sms || !levels))) return MCTP_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const int rc = check_update(textures[i], &sms[i], levels[i]);
+        if (rc != MCTP_OK) return rc;
+        if (sms[i].dtype != sms[0].dtype) return MCTP_EINVAL;
+    }
+    if (count == 0) return MCTP_OK;
+    cudaStream_t s = mctp::as_stream(stream);
+    const bool u8 = sms[0].dtype == MCTP_U8;
+    PadBatch b{};
+    size_t smem = 0;
+    auto flush = [&]() -> int {
+        if (b.count == 0) return MCTP_OK;
+        const int rc = u8 ? launch_pad_batch<uint8_t>(b, smem, s) : launch_pad_batch<uint16_t>(b, smem, s);
+        b.count = 0;
+        smem = 0;
+        return rc;
+    };
+    for (int i = 0; i < count; ++i) {
+        const mctp_slicemap &sm = sms[i];
+        const int k = levels[i];
+        const mctp_atlas_texture *t = textures[i];
+        const int64_t pitch = int64_t(sm.tiles_x[k]) * sm.dims[k][0];
+        const size_t row_bytes = (size_t(pitch) * size_t(mctp::elem_size(sm.dtype)) + 15) / 16 * 16;
+        const int rpb = pad_rows_per_block(row_bytes);
+        if (row_bytes * size_t(rpb) > 200 * 1024) return MCTP_ESIZE;
+        const int64_t blocks = (t->height + rpb - 1) / rpb;
+        if (b.count == kPadBatch || int64_t(b.first[b.count]) + blocks > 0x7fffffff) {
+            const int rc = flush();
+            if (rc != MCTP_OK) return rc;
+        }
+        PadItem &it = b.item[b.count];
+        it.atlas = sm.atlas[k];
+        it.surf = t->surf;
+        it.pitch = pitch;
+        it.mx = sm.dims[k][0];
+        it.my = sm.dims[k][1];
+        it.width = int32_t(t->width);
+        it.height = int32_t(t->height);
+        it.rows_per_block = rpb;
+        b.first[b.count + 1] = b.first[b.count] + int32_t(blocks);
+        ++b.count;
+        smem = std::max(smem, row_bytes * size_t(rpb));
+    }
+    return flush();
 }
 
 extern "C" int mctp_atlas_texture_destroy(mctp_atlas_texture *t)

@@ -115,6 +115,10 @@ __global__ void __launch_bounds__(kSelThreads)
     __shared__ BlockScratch sc;
     __shared__ int sh_T;
     const int tid = threadIdx.x;
+    // block i selects for histogram i of a batch (a single call launches one block)
+    if (hist) hist += int64_t(blockIdx.x) * nbins;
+    keep += int64_t(blockIdx.x) * nbins;
+    if (result) result += 4 * int64_t(blockIdx.x);
     int T = 0, iters = 0, converged = 1;
 
     if (p.mode == MCTP_THR_EXPLICIT) {
@@ -289,17 +293,38 @@ MCTP_FAULT_READER(threshold)
 
 }  // namespace mctp
 
+namespace mctp {
+namespace {
+int check_select(const uint64_t *hist, int32_t nbins, const mctp_thr_params *p, const uint8_t *keep_lut,
+                 bool need_buffers = true)
+{
+    if (!p || (need_buffers && !keep_lut)) return MCTP_EINVAL;
+    if (nbins < 1 || nbins > 65536 || log2_exact(nbins) < 0) return MCTP_EINVAL;
+    if (p->mode < MCTP_THR_OTSU || p->mode > MCTP_THR_EXPLICIT) return MCTP_EUNSUPPORTED;
+    if (need_buffers && p->mode != MCTP_THR_EXPLICIT && !hist) return MCTP_EINVAL;
+    if (p->mode == MCTP_THR_ITS && p->its_max_iter < 1) return MCTP_EINVAL;
+    if (p->mode == MCTP_THR_TOPSLAB && p->topslab_kmin < 1) return MCTP_EINVAL;
+    return MCTP_OK;
+}
+}  // namespace
+}  // namespace mctp
+
 extern "C" int mctp_select_threshold(const uint64_t *hist, int32_t nbins, const mctp_thr_params *p,
                                      uint8_t *keep_lut, int32_t *result, void *stream)
 {
+    return mctp_select_threshold_batch(hist, 1, nbins, p, keep_lut, result, stream);
+}
+
+extern "C" int mctp_select_threshold_batch(const uint64_t *hist, int32_t count, int32_t nbins,
+                                           const mctp_thr_params *p, uint8_t *keep_lut, int32_t *result,
+                                           void *stream)
+{
     using namespace mctp;
-    if (!p || !keep_lut) return MCTP_EINVAL;
-    if (nbins < 1 || nbins > 65536 || log2_exact(nbins) < 0) return MCTP_EINVAL;
-    if (p->mode < MCTP_THR_OTSU || p->mode > MCTP_THR_EXPLICIT) return MCTP_EUNSUPPORTED;
-    if (p->mode != MCTP_THR_EXPLICIT && !hist) return MCTP_EINVAL;
-    if (p->mode == MCTP_THR_ITS && p->its_max_iter < 1) return MCTP_EINVAL;
-    if (p->mode == MCTP_THR_TOPSLAB && p->topslab_kmin < 1) return MCTP_EINVAL;
-    select_kernel<<<1, kSelThreads, 0, as_stream(stream)>>>(
+    const int rc = check_select(hist, nbins, p, keep_lut, count != 0);
+    if (rc != MCTP_OK) return rc;
+    if (count < 0 || int64_t(count) * nbins > (int64_t(1) << 31)) return MCTP_EINVAL;
+    if (count == 0) return MCTP_OK;
+    select_kernel<<<unsigned(count), kSelThreads, 0, as_stream(stream)>>>(
         reinterpret_cast<const unsigned long long *>(hist), nbins, *p, keep_lut, result);
     return launch_status();
 }

@@ -31,3 +31,13 @@ def test_threaded_histogram_adds_up(orc):
     zs = np.linspace(0, 37, 6).astype(int)
     parts = [orc.histogram(vol, 12, 4096, int(zs[i]), int(zs[i + 1])) for i in range(5)]
     assert np.array_equal(sum(p[0] for p in parts), whole) and sum(p[1] for p in parts) == ov
+
+
+def test_batch_launch_count():
+    """The batched pass: 3 batched prepare launches per 64 volumes, the keep
+    tables in one, a level-0 kernel per volume, 3 render kernels and one view
+    upload per 128 views."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.batch_launches_per_step(64, 768) == 3 + 1 + 64 + 3 + 6
+    assert bench.batch_launches_per_step(65, 1) == 6 + 1 + 65 + 3 + 1

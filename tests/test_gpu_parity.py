@@ -120,6 +120,36 @@ def test_select_threshold(env):
             assert np.array_equal(keep.cpu().numpy(), oracle.keep_threshold(nb, T)), name
 
 
+def test_select_threshold_batch(env):
+    """One launch for many histograms: row i equals the single-histogram
+    selection of row i (which the test above pins to the oracle)."""
+    mctp, oracle, phantom, dev = env
+    rng = np.random.default_rng(11)
+    for nb, count in ((256, 64), (4096, 5), (1, 3), (16, 1)):
+        h = rng.integers(0, 1000, size=(count, nb)).astype(np.uint64)
+        h[0, :] = 0                                   # an empty histogram
+        if count > 2:
+            h[2, :] = 0
+            h[2, nb // 2] = 7                         # a single occupied bin
+        g = up(h, dev)
+        for mode, kw in (("otsu", {}), ("its", dict(its_max_iter=3)), ("topslab", dict(topslab_kmin=2)),
+                         ("explicit", dict(explicit_T=nb // 3))):
+            keep, res = mctp.select_threshold_batch(g, mode, **kw)
+            for i in range(count):
+                k1, r1 = mctp.select_threshold(g[i].contiguous(), mode=mode, **kw)
+                assert torch.equal(keep[i], k1), (nb, mode, i)
+                assert torch.equal(res[i], r1), (nb, mode, i)
+            if mode == "otsu":
+                for i in range(count):
+                    T, _ = oracle.otsu(h[i])
+                    assert int(res[i, 0]) == T
+    empty = torch.empty((0, 256), dtype=torch.uint64, device=dev)
+    keep, res = mctp.select_threshold_batch(empty)
+    assert keep.numel() == 0 and res.numel() == 0
+    with pytest.raises(ValueError):
+        mctp.select_threshold_batch(g, keep=torch.empty(1, dtype=torch.uint8, device=dev))
+
+
 # ------------------------------------------------------------------- filter
 
 @pytest.mark.parametrize("dtype,bits,nbins,shape", [(np.uint8, 8, 256, (13, 17, 19)), (np.uint8, 8, 16, (8, 8, 64)),
