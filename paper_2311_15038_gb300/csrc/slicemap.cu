@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kSmThreads, 4) slicemap_level0_kernel(L0Args<T
 constexpr int kRowsWarps = 8;
 constexpr int kRowsMaxCols = 1024;     // source row bytes the kernel takes
 constexpr int kRowsMaxYZ = 4096;       // level rows / slices the tables take
-constexpr int kRowsScratch = 1028;     // u32 per warp: column sums (80 B per lane), then E[0..nx] from word 3
+constexpr int kRowsScratch = 1064;     // u32 per warp: column sums (80 B per lane), then E (see below)
 
 struct RowsArgs {
     const uint8_t *vol;
@@ -601,7 +601,8 @@ __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(co
     const __half2 thr = bits_h2(lo | (lo << 16));
     uint32_t *mine = scratch + warp * kRowsScratch;
     uint4 *cols = reinterpret_cast<uint4 *>(mine) + 5 * lane;  // this lane's 32 column sums (80 bytes)
-    uint32_t *E = mine + 3;                                      // E[c], c = 0..nx; E + 4 is 16-byte aligned
+    // E[c], c = 0..nx, at word c + c / 32: a lane's 32 stores fall in 32 different banks
+    uint32_t *E = mine;
     const int64_t nrows = int64_t(a.mz) * a.my;
     const int64_t nwarps = int64_t(gridDim.x) * kRowsWarps;
     const bool active = 32 * lane < a.nx;
@@ -638,23 +639,19 @@ __global__ void __launch_bounds__(kRowsWarps * 32, 4) slicemap_rows_u8_kernel(co
         uint32_t run = incl - total;
         if (lane == 0) E[0] = 0u;
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            uint32_t p[4];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                run += v[2 * g + k] & 0xffffu;
-                p[2 * k] = run;
-                run += v[2 * g + k] >> 16;
-                p[2 * k + 1] = run;
-            }
-            reinterpret_cast<uint4 *>(E + 1 + 32 * lane)[g] = make_uint4(p[0], p[1], p[2], p[3]);
+        for (int i = 0; i < 16; ++i) {
+            const int c = 32 * lane + 2 * i + 1;
+            run += v[i] & 0xffffu;
+            E[c + (c >> 5)] = run;
+            run += v[i] >> 16;
+            E[c + 1 + ((c + 1) >> 5)] = run;
         }
         __syncwarp();
         uint8_t *out = atlas_ptr(a.atlas, a.pitch, a.tiles_x, a.mx, a.my, 0, y, z);
         const float rcp_lo = rcp_approx(float(wlo * R)), rcp_hi = rcp_approx(float((wlo + 1) * R));
         for (int x = lane; x < a.mx; x += 32) {
             const int c0 = xb[x], c1 = xb[x + 1];
-            const uint32_t sum = E[c1] - E[c0];
+            const uint32_t sum = E[c1 + (c1 >> 5)] - E[c0 + (c0 >> 5)];
             const int w = c1 - c0;
             const uint32_t q = div_round(sum, uint32_t(w * R), w == wlo ? rcp_lo : rcp_hi);
             if (in_range((out - a.atlas) + x, a.elems, kFaultAtlasWrite)) out[x] = uint8_t(q);
