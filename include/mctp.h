@@ -258,7 +258,10 @@ int mctp_build_slicemap(const void *vol, const mctp_volume_desc *d, const uint8_
  * vols[i], descs[i] and sms[i] (host arrays of count entries) as in
  * mctp_build_slicemap, keep table keep_luts[i nbins .. (i + 1) nbins) (device
  * uint8[count][nbins], or NULL for no filtering).  Every volume has the same
- * dtype.  The atlases are built volume by volume; the max grids of all
+ * dtype.  The atlases are built volume by volume, on `stream` and two
+ * streams forked from it (made once per host thread and device and kept;
+ * they join `stream` again before the call returns, so the work stays
+ * ordered on `stream` and records into a CUDA graph); the max grids of all
  * volumes' levels are filled in one launch afterwards.  Results equal those
  * of mctp_build_slicemap on each volume.
  * Errors: as mctp_build_slicemap for any volume (nothing is launched then);

@@ -983,6 +983,39 @@ MCTP_FAULT_READER(slicemap)
 
 namespace mctp {
 namespace {
+constexpr int kForks = 2;
+struct Forks {
+    int device = -1;
+    cudaStream_t stream[kForks] = {};
+    cudaEvent_t ev[kForks + 1] = {};
+};
+
+// This host thread's fork streams and events for the current device, made on
+// first use (nullptr when they cannot be made).
+Forks *thread_forks()
+{
+    thread_local Forks f[8];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 8) return nullptr;
+    Forks &k = f[dev];
+    if (k.device == dev) return &k;
+    bool ok = true;
+    for (int j = 0; j < kForks && ok; ++j)
+        ok = cudaStreamCreateWithFlags(&k.stream[j], cudaStreamNonBlocking) == cudaSuccess;
+    for (int j = 0; j <= kForks && ok; ++j) ok = cudaEventCreateWithFlags(&k.ev[j], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (int j = 0; j < kForks; ++j)
+            if (k.stream[j]) cudaStreamDestroy(k.stream[j]);
+        for (int j = 0; j <= kForks; ++j)
+            if (k.ev[j]) cudaEventDestroy(k.ev[j]);
+        k = Forks{};
+        return nullptr;
+    }
+    k.device = dev;
+    return &k;
+}
+
 int check_build(const void *vol, const mctp_volume_desc *d, const uint8_t *keep_lut, int32_t nbins,
                 const mctp_slicemap *sm)
 {
@@ -1032,15 +1065,40 @@ extern "C" int mctp_build_slicemap_batch(const void *const *vols, const mctp_vol
         if (descs[i].dtype != descs[0].dtype) return MCTP_EINVAL;
     }
     cudaStream_t s = as_stream(stream);
-    for (int i = 0; i < count; ++i) {
-        const uint8_t *keep = keep_luts ? keep_luts + int64_t(i) * nbins : nullptr;
-        const int rc = descs[i].dtype == MCTP_U8
-                           ? launch_slicemap(static_cast<const uint8_t *>(vols[i]), &descs[i], keep, nbins, &sms[i], s,
-                                             false)
-                           : launch_slicemap(static_cast<const uint16_t *>(vols[i]), &descs[i], keep, nbins, &sms[i],
-                                             s, false);
-        if (rc != MCTP_OK) return rc;
+    // The level-0 builds go round-robin to `s` and two streams forked from it,
+    // so that one build's last blocks overlap the next build's first ones; the
+    // forks join `s` again before the max grids (a capture into a CUDA graph
+    // records the same fork and join).  The fork streams and events are made
+    // once per host thread and device and kept; without them the builds stay
+    // on `s`.
+    Forks *fk = count > 1 ? thread_forks() : nullptr;
+    if (fk && cudaEventRecord(fk->ev[0], s) != cudaSuccess) {
+        // handles from a context that no longer exists: make new ones next time
+        cudaGetLastError();
+        *fk = Forks{};
+        fk = nullptr;
     }
+    const int nlanes = fk ? kForks + 1 : 1;
+    cudaStream_t lanes[kForks + 1] = {s};
+    int rc = MCTP_OK;
+    if (fk) {
+        for (int j = 0; j < kForks; ++j) lanes[j + 1] = fk->stream[j];
+        for (int j = 1; j < nlanes && rc == MCTP_OK; ++j)
+            if (cudaStreamWaitEvent(lanes[j], fk->ev[0], 0) != cudaSuccess) rc = MCTP_ECUDA;
+    }
+    for (int i = 0; i < count && rc == MCTP_OK; ++i) {
+        const uint8_t *keep = keep_luts ? keep_luts + int64_t(i) * nbins : nullptr;
+        cudaStream_t li = lanes[i % nlanes];
+        rc = descs[i].dtype == MCTP_U8
+                 ? launch_slicemap(static_cast<const uint8_t *>(vols[i]), &descs[i], keep, nbins, &sms[i], li, false)
+                 : launch_slicemap(static_cast<const uint16_t *>(vols[i]), &descs[i], keep, nbins, &sms[i], li, false);
+    }
+    // join the forks (also after an error, so that no fork is left outside s)
+    for (int j = 1; j < nlanes; ++j) {
+        if (cudaEventRecord(fk->ev[j], lanes[j]) != cudaSuccess || cudaStreamWaitEvent(s, fk->ev[j], 0) != cudaSuccess)
+            rc = MCTP_ECUDA;
+    }
+    if (rc != MCTP_OK) return rc;
     return descs[0].dtype == MCTP_U8 ? launch_maxgrid_batch<uint8_t>(sms, count, s)
                                      : launch_maxgrid_batch<uint16_t>(sms, count, s);
 }

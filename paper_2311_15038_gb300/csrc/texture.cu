@@ -67,14 +67,16 @@ __device__ __forceinline__ void pad_rows(const T *__restrict__ atlas, int64_t pi
     __syncthreads();
     const int cw = mx + 2;
     const float inv = 1.0f / float(cw);
+    const T *sh = reinterpret_cast<const T *>(sh_row_bytes);
+    const int st = int(stride);  // staged rows hold at most 200 KB
     for (int X = threadIdx.x; X < width; X += blockDim.x) {
         int col = int(float(X) * inv);
         if (col * cw > X) --col;
         else if ((col + 1) * cw <= X) ++col;
-        const int lx = min(max(X - col * cw - 1, 0), mx - 1);
-        for (int k = 0; k < nrows; ++k)
-            surf2Dwrite<T>(reinterpret_cast<T *>(sh_row_bytes)[k * stride + col * mx + lx], surf, X * int(sizeof(T)),
-                           Y0 + k, cudaBoundaryModeZero);
+        const int src = col * mx + min(max(X - col * cw - 1, 0), mx - 1);
+        surf2Dwrite<T>(sh[src], surf, X * int(sizeof(T)), Y0, cudaBoundaryModeZero);
+        for (int k = 1; k < nrows; ++k)
+            surf2Dwrite<T>(sh[k * st + src], surf, X * int(sizeof(T)), Y0 + k, cudaBoundaryModeZero);
     }
 }
 
