@@ -2,8 +2,8 @@
 every main index of the histogram, filter, slicemap and render kernels is
 tested against the extent of the buffer it addresses, and an index outside
 sets a bit in a device status word instead of being accessed.  Here the
-self-test sets and clears its bit, and the parity, batched and texture tests
-run again against the checked library in a child process, each ending with a
+self-test sets and clears its bit, and the parity, batched, texture and
+batched-preparation tests run again against the checked library in a child process, each ending with a
 check that no bit is set (tests/conftest.py)."""
 import os
 import subprocess
@@ -49,7 +49,8 @@ def test_parity_cases_under_the_checked_build():
     env = _env()
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
            os.path.join(ROOT, "tests", "test_gpu_parity.py"), os.path.join(ROOT, "tests", "test_gpu_batch.py"),
-           os.path.join(ROOT, "tests", "test_gpu_texture.py"), "-k", "not fullsize"]
+           os.path.join(ROOT, "tests", "test_gpu_texture.py"), os.path.join(ROOT, "tests", "test_gpu_prepare_batch.py"),
+           "-k", "not fullsize"]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=3000, cwd=ROOT)
     print(r.stdout[-2000:])
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
