@@ -3,8 +3,8 @@ every main index of the histogram, filter, slicemap and render kernels is
 tested against the extent of the buffer it addresses, and an index outside
 sets a bit in a device status word instead of being accessed.  Here the
 self-test sets and clears its bit, and the parity, batched, texture and
-batched-preparation tests run again against the checked library in a child process, each ending with a
-check that no bit is set (tests/conftest.py)."""
+batched-preparation tests run again against the checked library in a child
+process, each ending with a check that no bit is set (tests/conftest.py)."""
 import os
 import subprocess
 import sys
