@@ -724,12 +724,61 @@ __device__ __forceinline__ void maxgrid_row(const T *__restrict__ atlas, int64_t
     }
 }
 
+
+// Block `block` of a level's max grid with 32-bit loads: 4 u8 or 2 u16
+// columns per word (SIMD byte / halfword maxima), 64 words by 4 row groups
+// per 256 threads, so a thread makes about 20 loads per cell row instead of
+// 81; needs mx and the atlas pitch in whole words and a 4-byte-aligned atlas.
+template <typename T>
+__device__ __forceinline__ void maxgrid_row_vec(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx,
+                                                int my, int mz, uint16_t *__restrict__ grid, int gx, int gy, int block,
+                                                uint32_t *colmax)
+{
+    constexpr int c = MCTP_MAXGRID_CELL;
+    constexpr int EPW = 4 / int(sizeof(T));
+    const int cy = block % gy, cz = block / gy;
+    const int z0 = cz * c, z1 = min(cz * c + c, mz - 1), y0 = cy * c, y1 = min(cy * c + c, my - 1);
+    const int nw = mx / EPW;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    uint32_t *part = colmax + mx;  // [4][nw]
+    for (int w = tx; w < nw; w += 64) {
+        uint32_t m = 0;
+        for (int z = z0; z <= z1; ++z) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(
+                atlas_ptr(const_cast<T *>(atlas), pitch, tiles_x, mx, my, w * EPW, 0, z));
+            const int64_t wp = pitch / EPW;
+            for (int y = y0 + ty; y <= y1; y += 4) {
+                const uint32_t v = __ldg(row + int64_t(y) * wp);
+                m = sizeof(T) == 1 ? __vmaxu4(m, v) : __vmaxu2(m, v);
+            }
+        }
+        part[ty * nw + w] = m;
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        uint32_t m = part[w];
+        for (int k = 1; k < 4; ++k) m = sizeof(T) == 1 ? __vmaxu4(m, part[k * nw + w]) : __vmaxu2(m, part[k * nw + w]);
+        for (int e = 0; e < EPW; ++e) colmax[w * EPW + e] = sizeof(T) == 1 ? (m >> (8 * e)) & 0xffu : (m >> (16 * e)) & 0xffffu;
+    }
+    __syncthreads();
+    for (int cx = threadIdx.x; cx < gx; cx += blockDim.x) {
+        uint32_t m = 0;
+        const int x1 = min(cx * c + c, mx - 1);
+        for (int x = cx * c; x <= x1; ++x) m = max(m, colmax[x]);
+        grid[(int64_t(cz) * gy + cy) * gx + cx] = uint16_t(m);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) maxgrid_kernel(const T *__restrict__ atlas, int64_t pitch, int tiles_x, int mx,
-                                                      int my, int mz, uint16_t *__restrict__ grid, int gx, int gy)
+                                                      int my, int mz, uint16_t *__restrict__ grid, int gx, int gy,
+                                                      int vec)
 {
     extern __shared__ uint32_t colmax[];
-    maxgrid_row<T>(atlas, pitch, tiles_x, mx, my, mz, grid, gx, gy, int(blockIdx.x), colmax);
+    if (vec)
+        maxgrid_row_vec<T>(atlas, pitch, tiles_x, mx, my, mz, grid, gx, gy, int(blockIdx.x), colmax);
+    else
+        maxgrid_row<T>(atlas, pitch, tiles_x, mx, my, mz, grid, gx, gy, int(blockIdx.x), colmax);
 }
 
 // The max grids of up to kGridBatch levels (of one element type) in one
@@ -741,6 +790,7 @@ struct MaxgridItem {
     uint16_t *grid;
     int64_t pitch;
     int32_t tiles_x, mx, my, mz, gx, gy;
+    int32_t vec;  // maxgrid_row_vec applies (see maxgrid_vec_ok)
 };
 struct MaxgridBatch {
     int32_t count;
@@ -759,8 +809,12 @@ __global__ void __launch_bounds__(256) maxgrid_batch_kernel(const __grid_constan
         else hi = mid - 1;
     }
     const MaxgridItem &it = b.item[lo];
-    maxgrid_row<T>(static_cast<const T *>(it.atlas), it.pitch, it.tiles_x, it.mx, it.my, it.mz, it.grid, it.gx,
-                   it.gy, int(blockIdx.x) - b.first[lo], colmax);
+    if (it.vec)
+        maxgrid_row_vec<T>(static_cast<const T *>(it.atlas), it.pitch, it.tiles_x, it.mx, it.my, it.mz, it.grid, it.gx,
+                           it.gy, int(blockIdx.x) - b.first[lo], colmax);
+    else
+        maxgrid_row<T>(static_cast<const T *>(it.atlas), it.pitch, it.tiles_x, it.mx, it.my, it.mz, it.grid, it.gx,
+                       it.gy, int(blockIdx.x) - b.first[lo], colmax);
 }
 
 // Zero the tiles of an atlas that hold no slice.
@@ -780,20 +834,36 @@ int zero_unused_tiles(void *atlas, int esize, int mx, int my, int mz, int tx, in
     return MCTP_OK;
 }
 
+// Whether level k takes the 32-bit-load max grid, and the shared memory its
+// blocks need either way.
+template <typename T>
+bool maxgrid_vec_ok(const mctp_slicemap *sm, int k, size_t &smem)
+{
+    constexpr int EPW = 4 / int(sizeof(T));
+    const int mx = sm->dims[k][0];
+    const int64_t pitch = int64_t(sm->tiles_x[k]) * mx;
+    const size_t vsmem = size_t(mx) * sizeof(uint32_t) + size_t(4) * (size_t(mx) + 3) * sizeof(uint32_t);
+    const bool vec = mx % EPW == 0 && pitch % EPW == 0 && (reinterpret_cast<uintptr_t>(sm->atlas[k]) & 3) == 0 &&
+                     vsmem <= 200 * 1024;
+    smem = vec ? vsmem : size_t(mx) * sizeof(uint32_t);
+    return vec;
+}
+
 template <typename T>
 int launch_maxgrid(const mctp_slicemap *sm, int k, cudaStream_t s)
 {
     const int c = MCTP_MAXGRID_CELL;
     const int mx = sm->dims[k][0], my = sm->dims[k][1], mz = sm->dims[k][2];
     const int gx = (mx + c - 1) / c, gy = (my + c - 1) / c, gz = (mz + c - 1) / c;
-    const size_t smem = size_t(mx) * sizeof(uint32_t);
+    size_t smem = 0;
+    const bool vec = maxgrid_vec_ok<T>(sm, k, smem);
     if (smem > 200 * 1024) return MCTP_EUNSUPPORTED;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(maxgrid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return MCTP_ECUDA;
     maxgrid_kernel<T><<<unsigned(int64_t(gy) * gz), 256, smem, s>>>(
         static_cast<const T *>(sm->atlas[k]), int64_t(sm->tiles_x[k]) * mx, sm->tiles_x[k], mx, my, mz,
-        static_cast<uint16_t *>(sm->maxgrid[k]), gx, gy);
+        static_cast<uint16_t *>(sm->maxgrid[k]), gx, gy, vec ? 1 : 0);
     return launch_status();
 }
 
@@ -932,7 +1002,9 @@ int launch_maxgrid_batch(const mctp_slicemap *sms, int count, cudaStream_t s)
             const int c = MCTP_MAXGRID_CELL;
             const int mx = sm->dims[k][0], my = sm->dims[k][1], mz = sm->dims[k][2];
             const int gx = (mx + c - 1) / c, gy = (my + c - 1) / c, gz = (mz + c - 1) / c;
-            if (size_t(mx) * sizeof(uint32_t) > 200 * 1024) return MCTP_EUNSUPPORTED;
+            size_t need = 0;
+            const bool vec = maxgrid_vec_ok<T>(sm, k, need);
+            if (need > 200 * 1024) return MCTP_EUNSUPPORTED;
             if (b.count == kGridBatch || int64_t(b.first[b.count]) + int64_t(gy) * gz > 0x7fffffff) {
                 const int rc = flush();
                 if (rc != MCTP_OK) return rc;
@@ -943,9 +1015,10 @@ int launch_maxgrid_batch(const mctp_slicemap *sms, int count, cudaStream_t s)
             it.pitch = int64_t(sm->tiles_x[k]) * mx;
             it.tiles_x = sm->tiles_x[k];
             it.mx = mx; it.my = my; it.mz = mz; it.gx = gx; it.gy = gy;
+            it.vec = vec ? 1 : 0;
             b.first[b.count + 1] = b.first[b.count] + gy * gz;
             ++b.count;
-            smem = std::max(smem, size_t(mx) * sizeof(uint32_t));
+            smem = std::max(smem, need);
         }
     }
     return flush();

@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(kSurfThreads) atlas_pad_batch_kernel(const __g
                 it.rows_per_block, int(blockIdx.x) - b.first[lo], sh_row_bytes);
 }
 
-// Rows per block for staged rows of row_bytes: up to 4 while they fit 48 KB.
+// Rows per block for staged rows of row_bytes: 8 for short rows (<= 6 KB, launched
+// with 256 threads), else up to 4 while they fit 48 KB.
 int pad_rows_per_block(size_t row_bytes)
 {
-    return int(std::max<size_t>(1, std::min<size_t>(4, (48 * 1024) / row_bytes)));
+    return row_bytes <= 6 * 1024 ? 8 : int(std::max<size_t>(1, std::min<size_t>(4, (48 * 1024) / row_bytes)));
 }
 
 int texture_geometry(const mctp_slicemap *sm, int32_t level, int64_t &w, int64_t &h)
@@ -208,7 +209,8 @@ int launch_pad_batch(const PadBatch &b, size_t smem, cudaStream_t s)
         cudaFuncSetAttribute(atlas_pad_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
             cudaSuccess)
         return MCTP_ECUDA;
-    atlas_pad_batch_kernel<T><<<unsigned(b.first[b.count]), kSurfThreads, smem, s>>>(b);
+    const int threads = b.item[0].rows_per_block >= 8 ? 256 : kSurfThreads;
+    atlas_pad_batch_kernel<T><<<unsigned(b.first[b.count]), threads, smem, s>>>(b);
     return mctp::launch_status();
 }
 }  // namespace
