@@ -843,8 +843,10 @@ bool maxgrid_vec_ok(const mctp_slicemap *sm, int k, size_t &smem)
     const int mx = sm->dims[k][0];
     const int64_t pitch = int64_t(sm->tiles_x[k]) * mx;
     const size_t vsmem = size_t(mx) * sizeof(uint32_t) + size_t(4) * (size_t(mx) + 3) * sizeof(uint32_t);
-    const bool vec = mx % EPW == 0 && pitch % EPW == 0 && (reinterpret_cast<uintptr_t>(sm->atlas[k]) & 3) == 0 &&
-                     vsmem <= 200 * 1024;
+    // u8 only: with two u16 columns per word a thread makes about as many
+    // loads as the one-column kernel, which measured faster on u16 levels
+    const bool vec = sizeof(T) == 1 && mx % EPW == 0 && pitch % EPW == 0 &&
+                     (reinterpret_cast<uintptr_t>(sm->atlas[k]) & 3) == 0 && vsmem <= 200 * 1024;
     smem = vec ? vsmem : size_t(mx) * sizeof(uint32_t);
     return vec;
 }
