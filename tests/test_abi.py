@@ -368,3 +368,58 @@ def test_normal_library_is_not_the_checked_build(lib):
     bits = ctypes.c_uint32(7)
     assert lib.mctp_checked_status(ctypes.byref(bits), 0) == -2 and bits.value == 0
     assert lib.mctp_checked_selftest(None) == -2
+
+
+def test_batched_preparation_rejects(lib):
+    """The batched entry points check counts, pointers, dtypes and bins on the
+    host; an empty batch launches nothing and succeeds."""
+    from paper_2311_15038_gb300 import _lib
+    d8, d16 = _desc(), _desc(dtype=2, bits=12)
+    vols = (ctypes.c_void_p * 2)(0x10000, 0x20000)
+    mixed = (_lib.VolumeDesc * 2)(d8, d16)
+    same = (_lib.VolumeDesc * 2)(d8, d8)
+    # histograms
+    assert lib.mctp_build_histogram_batch(vols, same, -1, 256, FAKE, FAKE, None) == -1
+    assert lib.mctp_build_histogram_batch(None, same, 2, 256, FAKE, FAKE, None) == -1
+    assert lib.mctp_build_histogram_batch(vols, same, 2, 256, None, FAKE, None) == -1
+    assert lib.mctp_build_histogram_batch(vols, mixed, 2, 256, FAKE, FAKE, None) == -1
+    assert lib.mctp_build_histogram_batch(vols, same, 2, 100, FAKE, FAKE, None) == -1
+    assert lib.mctp_build_histogram_batch(vols, same, 2, 512, FAKE, FAKE, None) == -1   # > 2^bits bins
+    assert lib.mctp_build_histogram_batch(None, None, 0, 256, None, None, None) == 0
+    # keep tables
+    p = _lib.ThrParams(0, 0, 256, 0, 1)
+    assert lib.mctp_select_threshold_batch(FAKE, -1, 256, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold_batch(FAKE, 2, 3, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold_batch(None, 2, 256, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold_batch(FAKE, 2, 256, ctypes.byref(p), None, None, None) == -1
+    assert lib.mctp_select_threshold_batch(FAKE, 1 << 20, 4096, ctypes.byref(p), FAKE, None, None) == -1
+    assert lib.mctp_select_threshold_batch(None, 0, 256, ctypes.byref(p), None, None, None) == 0
+    # slicemaps
+    sm = (_lib.SlicemapDesc * 2)()
+    assert lib.mctp_build_slicemap_batch(vols, same, None, 0, sm, -1, None) == -1
+    assert lib.mctp_build_slicemap_batch(None, same, None, 0, sm, 2, None) == -1
+    assert lib.mctp_build_slicemap_batch(vols, same, None, 0, None, 2, None) == -1
+    assert lib.mctp_build_slicemap_batch(vols, same, None, 0, sm, 2, None) < 0          # empty slicemap descs
+    assert lib.mctp_build_slicemap_batch(None, None, None, 0, None, 0, None) == 0
+    # textures
+    lv = (_lib.C_I32 * 2)(0, 0)
+    tex = (ctypes.c_void_p * 2)(None, None)
+    assert lib.mctp_atlas_texture_update_batch(tex, sm, lv, -1, None) == -1
+    assert lib.mctp_atlas_texture_update_batch(None, sm, lv, 2, None) == -1
+    assert lib.mctp_atlas_texture_update_batch(tex, sm, lv, 2, None) == -1              # null textures
+    assert lib.mctp_atlas_texture_update_batch(None, None, None, 0, None) == 0
+
+
+def test_batched_bindings_refuse_host_tensors():
+    """The Python bindings refuse CPU tensors and malformed shapes before the library is called."""
+    torch = pytest.importorskip("torch")
+    import paper_2311_15038_gb300 as mctp
+    v = torch.zeros((2, 3, 4), dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        mctp.build_histogram_batch([v], 8, 256)
+    with pytest.raises(ValueError):
+        mctp.build_histogram_batch([], 8, 256)
+    with pytest.raises(ValueError):
+        mctp.select_threshold_batch(torch.zeros((2, 256), dtype=torch.int64))
+    with pytest.raises(ValueError):
+        mctp.build_slicemap_batch([v], 8, [])
