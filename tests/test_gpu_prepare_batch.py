@@ -87,12 +87,13 @@ def _slicemaps(mctp, vols, dims_of, bits, dev, maxgrid=True):
     return out
 
 
-@pytest.mark.parametrize("count", [3, 70])
+@pytest.mark.parametrize("count", [1, 2, 3, 70])
 @pytest.mark.parametrize("filtered", [True, False])
 def test_slicemap_batch_equals_single(env, count, filtered):
     """u8 volumes take the row kernel (one level); atlases and max grids equal
     per-volume builds, the max grids of all volumes coming from one launch
-    (two for 70 volumes)."""
+    (two for 70 volumes).  One volume stays on the caller's stream; from two
+    on the builds are spread over forked streams."""
     mctp, oracle, phantom, dev = env
     rng = np.random.default_rng(count + 7 * filtered)
     shapes = [tuple(int(x) for x in rng.integers(9, 40, size=3)) for _ in range(count)]
